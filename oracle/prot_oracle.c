@@ -1,0 +1,416 @@
+/*
+ * prot_oracle.c -- plain, slow CPU oracle for the push-relabel additive
+ * approximation of Lahn, Raghvendra and Zhang, "A Push-Relabel Based Additive
+ * Approximation for Optimal Transport" (arXiv 2203.03732).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the package's smoke entry and the bench's
+ * CPU-baseline leg do.  It shares no code, header, table or constant with the
+ * CUDA library: it is written from the paper alone, as nested loops over
+ * plain arrays, in the order the paper states its steps.
+ *
+ * Units: every dual weight and rounded cost is kept as an integer multiple of
+ * eps (Sec. 2.1 says all duals stay integer multiples of eps), so
+ *   cb(b,a) = floor(c(b,a) / eps)            (Eq. 1, divided by eps)
+ *   admissible(a,b)  <=>  y(a) + y(b) == cb + 1   (slack 0, Sec. 2.1 / Eq. 2)
+ *   matched edge     <=>  y(a) + y(b) == cb       (Eq. 3)
+ * Rows are the vertices of B (the supply side whose free vertices form B'),
+ * columns the vertices of A.
+ *
+ * Pinned choices where the paper leaves a free hand (see the design notes):
+ *   - Step I's maximal matching uses the round rule: every still-active free
+ *     b proposes to the lowest-index admissible a that was not taken in an
+ *     earlier round of this phase; every a accepts its lowest-index proposer;
+ *     rounds repeat until nobody proposes.
+ *   - Completion matches the k-th free b (ascending) with the k-th free a
+ *     (ascending); duals are left unchanged.
+ *   - The stopping threshold is T = floor(eps * |B|) computed in FP64.
+ *
+ * Parity pins (all in the CPU test suite): brute force over permutations for
+ * n <= 8, an exact Hungarian solver cross-checked against scipy, the
+ * invariants (I1)/(I2) after every phase, Lemma 2.1, Lemma 3.1's additive
+ * bound and its dual certificate, Lemma 3.2's dual magnitude bound, the exact
+ * per-phase growth of Lemma 3.3, closed-form special cases (constant costs,
+ * zero diagonal, zero permutation), literal-rescan vs resume-pointer
+ * equivalence, and independence from the order in which B' is processed.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+#include "prot_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (1): rounding of costs to integer multiples of eps.                   */
+/* ------------------------------------------------------------------------ */
+
+/* cb = floor(C / eps) with an IEEE FP64 divide.  Costs must be finite and in
+ * [0, 1] (Sec. 1 assumes the costs are scaled so that the largest is 1).
+ * Returns 0, or -1 at the first invalid cost. */
+int or_quantise_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA,
+                    double eps, int32_t *cb)
+{
+    for (int32_t b = 0; b < nB; ++b) {
+        for (int32_t a = 0; a < nA; ++a) {
+            double c = C[(int64_t)b * ldc + a];
+            if (!(c >= 0.0 && c <= 1.0)) return -1;
+            cb[(int64_t)b * nA + a] = (int32_t)floor(c / eps);
+        }
+    }
+    return 0;
+}
+
+/* Same for FP32 costs: the float is first widened (exactly) to double. */
+int or_quantise_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA,
+                    double eps, int32_t *cb)
+{
+    for (int32_t b = 0; b < nB; ++b) {
+        for (int32_t a = 0; a < nA; ++a) {
+            double c = (double)C[(int64_t)b * ldc + a];
+            if (!(c >= 0.0 && c <= 1.0)) return -1;
+            cb[(int64_t)b * nA + a] = (int32_t)floor(c / eps);
+        }
+    }
+    return 0;
+}
+
+/* Termination threshold of Sec. 2.2 (|B'| <= eps n), for the unbalanced case
+ * with |B| <= |A| (Sec. 3.3, Lemma 3.5): T = floor(eps * |B|). */
+int32_t or_threshold(double eps, int32_t nB)
+{
+    return (int32_t)floor(eps * (double)nB);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2: the phase loop.                                                 */
+/* ------------------------------------------------------------------------ */
+
+static int admissible(const int32_t *cb, int32_t nA, const int32_t *y_b,
+                      const int32_t *y_a, int32_t b, int32_t a)
+{
+    return y_a[a] + y_b[b] == cb[(int64_t)b * nA + a] + 1;
+}
+
+/* Invariants (I1), (I2) and the matching's consistency.  Returns the number
+ * of violations found (0 when the state is eps-feasible). */
+int64_t or_check_state(const int32_t *cb, int32_t nB, int32_t nA,
+                       const int32_t *match_b, const int32_t *match_a,
+                       const int32_t *y_b, const int32_t *y_a)
+{
+    int64_t bad = 0;
+    for (int32_t b = 0; b < nB; ++b) {
+        int32_t a = match_b[b];
+        if (a >= 0 && (a >= nA || match_a[a] != b)) ++bad;
+        if (y_b[b] < 0) ++bad;                     /* (I1): y(b) >= 0 */
+    }
+    for (int32_t a = 0; a < nA; ++a) {
+        int32_t b = match_a[a];
+        if (b >= 0 && (b >= nB || match_b[b] != a)) ++bad;
+        if (y_a[a] > 0) ++bad;                     /* (I1): y(a) <= 0 */
+        if (b < 0 && y_a[a] != 0) ++bad;           /* (I1): free a has 0 */
+    }
+    for (int32_t b = 0; b < nB; ++b) {
+        for (int32_t a = 0; a < nA; ++a) {
+            int32_t s = y_a[a] + y_b[b];
+            int32_t c = cb[(int64_t)b * nA + a];
+            if (match_b[b] == a) {
+                if (s != c) ++bad;                 /* Eq. (3) */
+            } else {
+                if (s > c + 1) ++bad;              /* Eq. (2) */
+            }
+        }
+    }
+    return bad;
+}
+
+/*
+ * One run of the main routine of Sec. 2.2 on integer costs cb (row-major,
+ * nB x nA, nB <= nA).  Outputs the matching before completion and both dual
+ * vectors.  mode is a bit set of OR_MODE_*.
+ *
+ * Returns OR_OK, OR_ERR_NO_CONVERGENCE if phase_cap phases ran without
+ * reaching the threshold, OR_ERR_INVALID for bad sizes, OR_ERR_NOMEM.
+ */
+int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
+                  int32_t mode, int64_t phase_cap,
+                  int32_t *match_b, int32_t *match_a,
+                  int32_t *y_b, int32_t *y_a, or_stats *st,
+                  int32_t *ni_log, int64_t ni_log_cap)
+{
+    if (nB < 1 || nA < nB || T < 0) return OR_ERR_INVALID;
+    int32_t *F = (int32_t *)malloc(sizeof(int32_t) * nB);      /* B' */
+    int32_t *act = (int32_t *)malloc(sizeof(int32_t) * nB);    /* active */
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * nB);
+    int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * nB);   /* M' */
+    int32_t *ptr = (int32_t *)malloc(sizeof(int32_t) * nB);
+    int32_t *prop = (int32_t *)malloc(sizeof(int32_t) * nB);
+    int32_t *taken = (int32_t *)malloc(sizeof(int32_t) * nA);  /* round */
+    int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nA);
+    int32_t *mround = (int32_t *)malloc(sizeof(int32_t) * nB);
+    if (!F || !act || !nxt || !mate || !ptr || !prop || !taken || !best || !mround) {
+        free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
+        free(taken); free(best); free(mround);
+        return OR_ERR_NOMEM;
+    }
+    memset(st, 0, sizeof(*st));
+    st->threshold = T;
+
+    /* Initialisation (Sec. 2.2): y(b) = eps, y(a) = 0, M empty. */
+    for (int32_t b = 0; b < nB; ++b) { y_b[b] = 1; match_b[b] = -1; }
+    for (int32_t a = 0; a < nA; ++a) { y_a[a] = 0; match_a[a] = -1; best[a] = INT32_MAX; }
+
+    int rc = OR_OK;
+    for (;;) {
+        /* B' = free vertices of B. */
+        int32_t nf = 0;
+        for (int32_t b = 0; b < nB; ++b)
+            if (match_b[b] < 0) F[nf++] = b;
+        if (nf <= T) { st->free_at_stop = nf; break; }
+        if (st->phases >= phase_cap) { st->free_at_stop = nf; rc = OR_ERR_NO_CONVERGENCE; break; }
+        if (ni_log && st->phases < ni_log_cap) ni_log[st->phases] = nf;
+        st->phases += 1;
+        st->sum_ni += nf;
+
+        /* Step (I): maximal matching M' in G'(A' u B', E') by rounds. */
+        for (int32_t a = 0; a < nA; ++a) taken[a] = 0;
+        for (int32_t i = 0; i < nf; ++i) {
+            int32_t b = F[i];
+            mate[b] = -1; ptr[b] = 0; mround[b] = 0;
+        }
+        int32_t nact = nf;
+        for (int32_t i = 0; i < nf; ++i) act[i] = F[i];
+        if (mode & OR_MODE_REVERSE) {
+            for (int32_t i = 0; i < nact / 2; ++i) {
+                int32_t t = act[i]; act[i] = act[nact - 1 - i]; act[nact - 1 - i] = t;
+            }
+        }
+
+        if (mode & OR_MODE_SEQUENTIAL) {
+            /* The paper's sequential greedy (Lemma 3.4): process B' in
+             * ascending order, give each b its first admissible a that is not
+             * yet matched in M'.  A different, equally valid maximal M'. */
+            for (int32_t i = 0; i < nf; ++i) {
+                int32_t b = F[i];
+                for (int32_t a = 0; a < nA; ++a) {
+                    st->scanned += 1;
+                    if (!taken[a] && admissible(cb, nA, y_b, y_a, b, a)) {
+                        taken[a] = 1; mate[b] = a; break;
+                    }
+                }
+            }
+            st->rounds += 1;
+        } else {
+            int32_t r = 0;
+            for (;;) {
+                ++r;
+                /* Proposals of round r, all made against the taken[] state
+                 * left by rounds 1..r-1. */
+                int32_t nprop = 0;
+                for (int32_t i = 0; i < nact; ++i) {
+                    int32_t b = act[i];
+                    int32_t start = (mode & OR_MODE_LITERAL) ? 0 : ptr[b];
+                    int32_t p = -1;
+                    for (int32_t a = start; a < nA; ++a) {
+                        st->scanned += 1;
+                        if (taken[a] == 0 && admissible(cb, nA, y_b, y_a, b, a)) { p = a; break; }
+                    }
+                    prop[b] = p;
+                    if (p >= 0) {
+                        ++nprop;
+                        if (b < best[p]) best[p] = b;
+                    } else {
+                        ptr[b] = nA;
+                    }
+                }
+                if (nprop == 0) break;
+                st->rounds += 1;
+                /* Acceptance: each a takes its lowest-index proposer. */
+                int32_t nn = 0;
+                for (int32_t i = 0; i < nact; ++i) {
+                    int32_t b = act[i];
+                    int32_t p = prop[b];
+                    if (p < 0) continue;              /* b leaves: no edge */
+                    if (best[p] == b) {
+                        mate[b] = p; mround[b] = r;
+                    } else {
+                        ptr[b] = p + 1;               /* resume after p */
+                        nxt[nn++] = b;
+                    }
+                }
+                for (int32_t i = 0; i < nact; ++i) {
+                    int32_t b = act[i];
+                    int32_t p = prop[b];
+                    if (p >= 0) { taken[p] = r; best[p] = INT32_MAX; }
+                }
+                nact = nn;
+                for (int32_t i = 0; i < nn; ++i) act[i] = nxt[i];
+                if (nact == 0) break;
+            }
+        }
+
+        /* Step (II): add M' to M, delete M'' (the old edges of re-matched a).
+         * Lemma 2.1: the result is a matching and no matched a becomes free. */
+        for (int32_t i = 0; i < nf; ++i) {
+            int32_t b = F[i];
+            int32_t a = mate[b];
+            if (a < 0) continue;
+            int32_t old = match_a[a];
+            if (old >= 0) match_b[old] = -1;
+            match_a[a] = b;
+            match_b[b] = a;
+        }
+        /* Step (III): (a) y(a) -= eps for a matched in M';
+         *             (b) y(b) += eps for b in B' free with respect to M'. */
+        for (int32_t i = 0; i < nf; ++i) {
+            int32_t b = F[i];
+            if (mate[b] >= 0) y_a[mate[b]] -= 1;
+            else y_b[b] += 1;
+        }
+        if (mode & OR_MODE_CHECK)
+            st->violations += or_check_state(cb, nB, nA, match_b, match_a, y_b, y_a);
+    }
+
+    free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
+    free(taken); free(best); free(mround);
+    return rc;
+}
+
+/* Completion (Sec. 2.1, last paragraph): the remaining free vertices are
+ * matched arbitrarily; pinned here as the k-th free b with the k-th free a. */
+void or_complete(int32_t nB, int32_t nA, int32_t *match_b, int32_t *match_a)
+{
+    int32_t a = 0;
+    for (int32_t b = 0; b < nB; ++b) {
+        if (match_b[b] >= 0) continue;
+        while (a < nA && match_a[a] >= 0) ++a;
+        if (a >= nA) return;                       /* cannot happen: nB <= nA */
+        match_b[b] = a;
+        match_a[a] = b;
+    }
+}
+
+/* c(M) = sum over the matching of the ORIGINAL costs (Sec. 1), as an FP64
+ * Neumaier-compensated sum in ascending b. */
+static void neumaier_add(double *s, double *comp, double x)
+{
+    double t = *s + x;
+    if (fabs(*s) >= fabs(x)) *comp += (*s - t) + x;
+    else *comp += (x - t) + *s;
+    *s = t;
+}
+
+double or_cost_f64(const double *C, int64_t ldc, int32_t nB, const int32_t *match_b)
+{
+    double s = 0.0, comp = 0.0;
+    for (int32_t b = 0; b < nB; ++b)
+        neumaier_add(&s, &comp, C[(int64_t)b * ldc + match_b[b]]);
+    return s + comp;
+}
+
+double or_cost_f32(const float *C, int64_t ldc, int32_t nB, const int32_t *match_b)
+{
+    double s = 0.0, comp = 0.0;
+    for (int32_t b = 0; b < nB; ++b)
+        neumaier_add(&s, &comp, (double)C[(int64_t)b * ldc + match_b[b]]);
+    return s + comp;
+}
+
+/* Whole solve on FP64 costs: quantise, main routine, completion, cost. */
+int or_assign_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA, double eps,
+                  int32_t mode, int32_t *match_b, int32_t *match_a,
+                  int32_t *y_b, int32_t *y_a, double *cost, or_stats *st)
+{
+    if (nB < 1 || nA < nB || !(eps > 0.0 && eps < 1.0)) return OR_ERR_INVALID;
+    if (floor(1.0 / eps) > 32766.0) return OR_ERR_INVALID;
+    int32_t *cb = (int32_t *)malloc(sizeof(int32_t) * (size_t)nB * (size_t)nA);
+    if (!cb) return OR_ERR_NOMEM;
+    if (or_quantise_f64(C, ldc, nB, nA, eps, cb) != 0) { free(cb); return OR_ERR_INVALID; }
+    int32_t T = or_threshold(eps, nB);
+    int rc = or_assign_int(cb, nB, nA, T, mode, or_phase_cap(eps, nB), match_b, match_a,
+                           y_b, y_a, st, NULL, 0);
+    free(cb);
+    if (rc != OR_OK) return rc;
+    or_complete(nB, nA, match_b, match_a);
+    *cost = or_cost_f64(C, ldc, nB, match_b);
+    return OR_OK;
+}
+
+int or_assign_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA, double eps,
+                  int32_t mode, int32_t *match_b, int32_t *match_a,
+                  int32_t *y_b, int32_t *y_a, double *cost, or_stats *st)
+{
+    if (nB < 1 || nA < nB || !(eps > 0.0 && eps < 1.0)) return OR_ERR_INVALID;
+    if (floor(1.0 / eps) > 32766.0) return OR_ERR_INVALID;
+    int32_t *cb = (int32_t *)malloc(sizeof(int32_t) * (size_t)nB * (size_t)nA);
+    if (!cb) return OR_ERR_NOMEM;
+    if (or_quantise_f32(C, ldc, nB, nA, eps, cb) != 0) { free(cb); return OR_ERR_INVALID; }
+    int32_t T = or_threshold(eps, nB);
+    int rc = or_assign_int(cb, nB, nA, T, mode, or_phase_cap(eps, nB), match_b, match_a,
+                           y_b, y_a, st, NULL, 0);
+    free(cb);
+    if (rc != OR_OK) return rc;
+    or_complete(nB, nA, match_b, match_a);
+    *cost = or_cost_f32(C, ldc, nB, match_b);
+    return OR_OK;
+}
+
+/* A phase cap that valid input never reaches.  Each phase raises the total
+ * dual magnitude S = sum y(b) - sum y(a) by exactly |B'| > T (Lemma 3.3's
+ * argument, made exact in integer units), S starts at |B| and, by Lemma 3.2
+ * (|y| <= floor(1/eps) + 2 in eps units), ends at most 2|B|(floor(1/eps)+2).
+ * Hence phases <= |B|(2 floor(1/eps) + 3) / (T + 1). */
+int64_t or_phase_cap(double eps, int32_t nB)
+{
+    int64_t K = (int64_t)floor(1.0 / eps);
+    int64_t T = or_threshold(eps, nB);
+    return ((int64_t)nB * (2 * K + 3)) / (T + 1) + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact solver for the pins: the textbook shortest-augmenting-path          */
+/* Hungarian method with vertex potentials, O(nB^2 nA), for nB <= nA.        */
+/* ------------------------------------------------------------------------ */
+double or_hungarian(const double *C, int64_t ldc, int32_t nB, int32_t nA, int32_t *row_to_col)
+{
+    /* 1-based arrays; index 0 is the virtual root column. */
+    double *u = (double *)calloc((size_t)nB + 1, sizeof(double));
+    double *v = (double *)calloc((size_t)nA + 1, sizeof(double));
+    double *minv = (double *)malloc(sizeof(double) * ((size_t)nA + 1));
+    int32_t *p = (int32_t *)calloc((size_t)nA + 1, sizeof(int32_t));   /* row matched to column */
+    int32_t *way = (int32_t *)calloc((size_t)nA + 1, sizeof(int32_t));
+    char *used = (char *)malloc((size_t)nA + 1);
+    for (int32_t i = 1; i <= nB; ++i) {
+        p[0] = i;
+        int32_t j0 = 0;
+        for (int32_t j = 0; j <= nA; ++j) { minv[j] = DBL_MAX; used[j] = 0; }
+        do {
+            used[j0] = 1;
+            int32_t i0 = p[j0], j1 = 0;
+            double delta = DBL_MAX;
+            for (int32_t j = 1; j <= nA; ++j) {
+                if (used[j]) continue;
+                double cur = C[(int64_t)(i0 - 1) * ldc + (j - 1)] - u[i0] - v[j];
+                if (cur < minv[j]) { minv[j] = cur; way[j] = j0; }
+                if (minv[j] < delta) { delta = minv[j]; j1 = j; }
+            }
+            for (int32_t j = 0; j <= nA; ++j) {
+                if (used[j]) { u[p[j]] += delta; v[j] -= delta; }
+                else minv[j] -= delta;
+            }
+            j0 = j1;
+        } while (p[j0] != 0);
+        do {
+            int32_t j1 = way[j0];
+            p[j0] = p[j1];
+            j0 = j1;
+        } while (j0);
+    }
+    for (int32_t j = 1; j <= nA; ++j)
+        if (p[j] != 0) row_to_col[p[j] - 1] = j - 1;
+    double s = 0.0, comp = 0.0;
+    for (int32_t b = 0; b < nB; ++b)
+        neumaier_add(&s, &comp, C[(int64_t)b * ldc + row_to_col[b]]);
+    free(u); free(v); free(minv); free(p); free(way); free(used);
+    return s + comp;
+}

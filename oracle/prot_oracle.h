@@ -1,0 +1,51 @@
+/*
+ * prot_oracle.h -- the CPU oracle's own declarations (test infrastructure
+ * only; independent of the CUDA library's public header).
+ */
+#ifndef PROT_ORACLE_H
+#define PROT_ORACLE_H
+#include <stdint.h>
+
+#define OR_OK 0
+#define OR_ERR_INVALID (-1)
+#define OR_ERR_NO_CONVERGENCE (-4)
+#define OR_ERR_NOMEM (-7)
+
+/* mode bits of or_assign_int */
+#define OR_MODE_RESUME 0      /* resume pointer per b (default)             */
+#define OR_MODE_LITERAL 1     /* rescan every row from a = 0 in every round */
+#define OR_MODE_CHECK 2       /* check (I1)/(I2) after every phase          */
+#define OR_MODE_REVERSE 4     /* process B' in descending order             */
+#define OR_MODE_SEQUENTIAL 8  /* the paper's sequential greedy (Lemma 3.4)  */
+
+typedef struct {
+    int64_t phases;       /* phases executed                                  */
+    int64_t rounds;       /* rounds (with at least one proposal), all phases  */
+    int64_t scanned;      /* cost entries examined by the proposal scans      */
+    int64_t sum_ni;       /* sum over phases of |B'|                          */
+    int64_t violations;   /* invariant violations seen (OR_MODE_CHECK)        */
+    int32_t free_at_stop; /* |B'| when the loop stopped                      */
+    int32_t threshold;    /* T                                                */
+} or_stats;
+
+int or_quantise_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA, double eps, int32_t *cb);
+int or_quantise_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA, double eps, int32_t *cb);
+int32_t or_threshold(double eps, int32_t nB);
+int64_t or_phase_cap(double eps, int32_t nB);
+int64_t or_check_state(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *match_b,
+                       const int32_t *match_a, const int32_t *y_b, const int32_t *y_a);
+int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T, int32_t mode,
+                  int64_t phase_cap, int32_t *match_b, int32_t *match_a, int32_t *y_b,
+                  int32_t *y_a, or_stats *st, int32_t *ni_log, int64_t ni_log_cap);
+void or_complete(int32_t nB, int32_t nA, int32_t *match_b, int32_t *match_a);
+double or_cost_f64(const double *C, int64_t ldc, int32_t nB, const int32_t *match_b);
+double or_cost_f32(const float *C, int64_t ldc, int32_t nB, const int32_t *match_b);
+int or_assign_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA, double eps, int32_t mode,
+                  int32_t *match_b, int32_t *match_a, int32_t *y_b, int32_t *y_a, double *cost,
+                  or_stats *st);
+int or_assign_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA, double eps, int32_t mode,
+                  int32_t *match_b, int32_t *match_a, int32_t *y_b, int32_t *y_a, double *cost,
+                  or_stats *st);
+double or_hungarian(const double *C, int64_t ldc, int32_t nB, int32_t nA, int32_t *row_to_col);
+
+#endif
