@@ -251,6 +251,8 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
 
         /* Step (II): add M' to M, delete M'' (the old edges of re-matched a).
          * Lemma 2.1: the result is a matching and no matched a becomes free. */
+        if (mode & OR_MODE_CHECK)
+            for (int32_t a = 0; a < nA; ++a) best[a] = match_a[a] >= 0 ? 1 : 0;
         for (int32_t i = 0; i < nf; ++i) {
             int32_t b = F[i];
             int32_t a = mate[b];
@@ -267,8 +269,13 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
             if (mate[b] >= 0) y_a[mate[b]] -= 1;
             else y_b[b] += 1;
         }
-        if (mode & OR_MODE_CHECK)
+        if (mode & OR_MODE_CHECK) {
+            for (int32_t a = 0; a < nA; ++a) {
+                if (best[a] == 1 && match_a[a] < 0) ++st->violations;   /* Lemma 2.1 */
+                best[a] = INT32_MAX;
+            }
             st->violations += or_check_state(cb, nB, nA, match_b, match_a, y_b, y_a);
+        }
     }
 
     free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);

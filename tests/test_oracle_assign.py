@@ -1,0 +1,300 @@
+"""Pins for the assignment oracle (CPU only).
+
+Every check here ties the oracle to something other than itself: brute force
+over permutations, scipy's exact assignment solver, the paper's invariants
+(I1)/(I2) and Lemma 2.1 after every phase, the bounds of Lemma 3.1, 3.2 and
+Eq. (4), a hand-worked run of Sec. 2.2 (tests/golden), and closed forms.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_2203_03732_gb300 import workloads as W
+
+EPS_SET = [0.5, 0.3, 0.1, 0.05]
+
+
+def brute_force(C):
+    nB, nA = C.shape
+    best = math.inf
+    for perm in itertools.permutations(range(nA), nB):
+        s = math.fsum(C[b, perm[b]] for b in range(nB))
+        best = min(best, s)
+    return best
+
+
+def rand_costs(seed, nB, nA, kind="uniform"):
+    g = np.random.default_rng(seed)
+    if kind == "uniform":
+        C = g.random((nB, nA))
+    elif kind == "few":
+        C = g.integers(0, 4, size=(nB, nA)) / 3.0
+    else:
+        raise ValueError(kind)
+    return C
+
+
+# -------------------------------------------------------------------------
+# Exact solvers used as pins
+# -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(12))
+def test_hungarian_matches_brute_force(seed):
+    g = np.random.default_rng(seed)
+    nB = int(g.integers(1, 7))
+    nA = int(g.integers(nB, 8))
+    C = rand_costs(seed, nB, nA, "uniform" if seed % 2 else "few")
+    v, r2c = oracle.hungarian(C)
+    assert len(set(r2c.tolist())) == nB
+    assert abs(v - math.fsum(C[np.arange(nB), r2c])) < 1e-12
+    assert abs(v - brute_force(C)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(40, 40), (120, 120), (60, 97), (300, 300)])
+def test_hungarian_matches_scipy(shape):
+    from scipy.optimize import linear_sum_assignment
+    C = rand_costs(sum(shape), *shape)
+    v, _ = oracle.hungarian(C)
+    r, c = linear_sum_assignment(C)
+    assert abs(v - C[r, c].sum()) < 1e-9
+
+
+# -------------------------------------------------------------------------
+# Eq. (1)
+# -------------------------------------------------------------------------
+
+def test_quantise_hand_values():
+    C = np.array([[0.0, 1.0, 0.5, 0.2999], [0.25, 0.75, 0.099, 0.1]])
+    cb = oracle.quantise(C, 0.25)
+    assert cb.tolist() == [[0, 4, 2, 1], [1, 3, 0, 0]]
+    cb = oracle.quantise(C, 0.1)
+    # 1/0.1, 0.5/0.1, 0.1/0.1 all round to exact integers in FP64.
+    assert cb.tolist() == [[0, 10, 5, 2], [2, 7, 0, 1]]
+
+
+def test_quantise_matches_exact_floor_off_boundary():
+    """cb = floor(c/eps) exactly (rational arithmetic) wherever c/eps is not
+    within one rounding of an integer."""
+    g = np.random.default_rng(7)
+    C = g.random((20, 30))
+    for eps in (0.1, 0.01, 0.005, 0.3):
+        cb = oracle.quantise(C, eps)
+        for b in range(C.shape[0]):
+            for a in range(C.shape[1]):
+                q = Fraction(C[b, a]) / Fraction(eps)
+                fl = math.floor(q)
+                if q - fl > Fraction(1, 10**9) and (fl + 1) - q > Fraction(1, 10**9):
+                    assert cb[b, a] == fl
+
+
+def test_quantise_rejects_out_of_range():
+    for bad in (-1e-300, 1.0000000000000002, np.nan, np.inf):
+        C = np.zeros((2, 2))
+        C[1, 1] = bad
+        with pytest.raises(ValueError):
+            oracle.quantise(C, 0.1)
+
+
+def test_threshold():
+    assert oracle.threshold(0.01, 10000) == 100
+    assert oracle.threshold(0.1, 1000) == 100
+    assert oracle.threshold(0.005, 10000) == 50
+    assert oracle.threshold(0.3, 3) == 0
+    assert oracle.threshold(0.5, 3) == 1
+
+
+# -------------------------------------------------------------------------
+# Hand-worked run (tests/golden/assign_3x3_hand.txt)
+# -------------------------------------------------------------------------
+
+def test_golden_hand_run():
+    g = read_golden("assign_3x3_hand.txt")
+    eps = float(g["eps"][0][0])
+    C = np.array([[float(x) for x in row] for row in g["C"]])
+    r = oracle.assign(C, eps, mode=oracle.MODE_CHECK)
+    assert r["cbar"].tolist() == [[int(x) for x in row] for row in g["cbar"]]
+    assert r["threshold"] == int(g["threshold"][0][0])
+    assert r["stats"]["phases"] == int(g["phases"][0][0])
+    assert r["stats"]["rounds"] == int(g["rounds"][0][0])
+    assert r["row_to_col"].tolist() == [int(x) for x in g["row_to_col"][0]]
+    assert r["col_to_row"].tolist() == [int(x) for x in g["col_to_row"][0]]
+    assert r["y_row"].tolist() == [int(x) for x in g["y_row"][0]]
+    assert r["y_col"].tolist() == [int(x) for x in g["y_col"][0]]
+    assert r["cost"] == float(g["cost"][0][0])
+    assert r["stats"]["violations"] == 0
+
+
+# -------------------------------------------------------------------------
+# Closed forms
+# -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,k,eps", [(5, 0.55, 0.1), (7, 1.0, 0.25), (4, 0.0, 0.5), (9, 0.31, 0.05)])
+def test_constant_costs(n, k, eps):
+    """C == k: K = floor(k/eps) pure relabel phases, then one phase of n rounds
+    in which b_i takes a_i (lowest-index proposal and acceptance)."""
+    C = np.full((n, n), k)
+    K = int(math.floor(k / eps))
+    T = oracle.threshold(eps, n)
+    assert T < n
+    r = oracle.assign(C, eps, mode=oracle.MODE_CHECK)
+    assert r["stats"]["phases"] == K + 1
+    assert r["stats"]["rounds"] == n
+    assert r["row_to_col"].tolist() == list(range(n))
+    assert (r["y_row"] == K + 1).all()
+    assert (r["y_col"] == -1).all()
+    assert r["stats"]["violations"] == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 6, 33])
+def test_zero_diagonal(n):
+    C = 1.0 - np.eye(n)
+    r = oracle.assign(C, 0.1, mode=oracle.MODE_CHECK)
+    assert r["row_to_col"].tolist() == list(range(n))
+    assert r["stats"]["phases"] == 1 and r["stats"]["rounds"] == 1
+    assert (r["y_col"] == -1).all() and (r["y_row"] == 1).all()
+    assert r["cost"] == 0.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_zero_permutation(seed):
+    n = 17
+    pi = np.random.default_rng(seed).permutation(n)
+    C = np.ones((n, n))
+    C[np.arange(n), pi] = 0.0
+    r = oracle.assign(C, 0.2)
+    assert r["row_to_col"].tolist() == pi.tolist()
+    assert r["stats"]["phases"] == 1
+    assert r["cost"] == 0.0
+
+
+def test_single_vertex():
+    """n = 1: T = 0, the row relabels until y_b = cb + 1, then matches."""
+    for c, eps in ((0.73, 0.1), (0.0, 0.3), (1.0, 0.25)):
+        r = oracle.assign(np.array([[c]]), eps)
+        K = int(math.floor(c / eps))
+        assert r["stats"]["phases"] == K + 1
+        assert r["y_row"][0] == K + 1 and r["y_col"][0] == -1
+        assert r["row_to_col"][0] == 0
+
+
+# -------------------------------------------------------------------------
+# Bounds and invariants on random instances
+# -------------------------------------------------------------------------
+
+def _check_bounds(C, eps, r, opt=None):
+    nB, nA = C.shape
+    K = int(math.floor(1.0 / eps))
+    T = r["threshold"]
+    st = r["stats"]
+    yb, ya = r["y_row"].astype(np.int64), r["y_col"].astype(np.int64)
+    # perfect (row-complete) matching
+    assert len(set(r["row_to_col"].tolist())) == nB
+    assert (r["row_to_col"] >= 0).all()
+    assert st["free_at_stop"] <= T
+    # Lemma 3.2 (eps units): |y| <= floor(1/eps) + 2
+    assert yb.max() <= K + 2 and -ya.min() <= K + 2
+    # Lemma 3.3 made exact: the total dual magnitude grows by |B'| per phase.
+    assert yb.sum() - ya.sum() - nB == st["sum_ni"]
+    # Eq. (4) with the factor 2 the 2n vertices need; phase bound of Sec. 3.2.
+    assert st["sum_ni"] <= nB * (2 * K + 3)
+    assert st["phases"] <= oracle.phase_cap(eps, nB)
+    # Lemma 3.1 dual certificate: L = eps (sum y - |B|) <= OPT(cbar) <= OPT(c),
+    # and c(M) <= L + 2 eps |B| + T (completion edges cost at most 1).
+    L = eps * (yb.sum() + ya.sum() - nB)
+    assert r["cost"] <= L + 2 * eps * nB + T + 1e-9
+    if opt is not None:
+        assert L <= opt + 1e-9
+        assert opt - 1e-9 <= r["cost"] <= opt + 3 * eps * nB + 1e-9
+    return L
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_brute_force_bound_small(seed):
+    g = np.random.default_rng(100 + seed)
+    nB = int(g.integers(1, 8))
+    nA = int(g.integers(nB, 8))
+    C = rand_costs(seed, nB, nA, "uniform" if seed % 3 else "few")
+    opt = brute_force(C)
+    for eps in EPS_SET:
+        r = oracle.assign(C, eps, mode=oracle.MODE_CHECK)
+        assert r["stats"]["violations"] == 0
+        L = _check_bounds(C, eps, r, opt)
+        # L also bounds the rounded optimum (Lemma 3.1 with costs cbar).
+        cbar_opt = brute_force(r["cbar"].astype(np.float64) * eps)
+        assert L <= cbar_opt + 1e-9
+
+
+@pytest.mark.parametrize("n,eps,sq", [(60, 0.1, True), (150, 0.05, False), (200, 0.01, False),
+                                      (120, 0.005, False), (90, 0.3, True)])
+def test_invariants_every_phase_and_hungarian_bound(n, eps, sq):
+    C = W.assignment_sq_euclid_2d(n, n) if sq else W.assignment_euclid_2d(n, n)
+    r = oracle.assign(C, eps, mode=oracle.MODE_CHECK)
+    assert r["stats"]["violations"] == 0
+    opt, _ = oracle.hungarian(C)
+    _check_bounds(C, eps, r, opt)
+
+
+@pytest.mark.parametrize("nB,nA", [(30, 45), (64, 200), (1, 9)])
+def test_unbalanced(nB, nA):
+    """Sec. 3.3: |B| <= |A|; stops at <= eps|B| free; Lemma 3.5 bound."""
+    A, B = W.points_uniform(nA, nB, 2, 5)
+    C = W.pairwise_cost(A, B, squared=False)
+    for eps in (0.1, 0.02):
+        r = oracle.assign(C, eps, mode=oracle.MODE_CHECK)
+        assert r["stats"]["violations"] == 0
+        opt, _ = oracle.hungarian(C)
+        _check_bounds(C, eps, r, opt)
+
+
+# -------------------------------------------------------------------------
+# The round rule itself
+# -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_literal_rescan_equals_resume_pointer(seed):
+    n = 70
+    C = W.assignment_euclid_2d(n, seed) if seed % 2 else rand_costs(seed, n, n, "few")
+    for eps in (0.1, 0.02):
+        cb = oracle.quantise(C, eps)
+        T = oracle.threshold(eps, n)
+        r0 = oracle.assign_int(cb, T, mode=oracle.MODE_RESUME)
+        r1 = oracle.assign_int(cb, T, mode=oracle.MODE_LITERAL)
+        r2 = oracle.assign_int(cb, T, mode=oracle.MODE_REVERSE)
+        for k in ("match_b", "match_a", "y_b", "y_a"):
+            assert np.array_equal(r0[k], r1[k]) and np.array_equal(r0[k], r2[k])
+        for k in ("phases", "rounds", "sum_ni"):
+            assert r0["stats"][k] == r1["stats"][k] == r2["stats"][k]
+
+
+def test_sequential_greedy_is_valid_but_different():
+    """The paper's own sequential greedy (Lemma 3.4) gives another valid run:
+    same invariants and bounds, generally a different matching."""
+    n = 80
+    C = W.assignment_sq_euclid_2d(n, 3)
+    eps = 0.1
+    cb = oracle.quantise(C, eps)
+    T = oracle.threshold(eps, n)
+    rs = oracle.assign_int(cb, T, mode=oracle.MODE_SEQUENTIAL | oracle.MODE_CHECK)
+    rr = oracle.assign_int(cb, T, mode=oracle.MODE_CHECK)
+    assert rs["stats"]["violations"] == 0 and rr["stats"]["violations"] == 0
+    assert not np.array_equal(rs["match_b"], rr["match_b"])
+
+
+def test_cost_is_exactly_rounded_sum():
+    C = W.assignment_euclid_2d(500, 1)
+    r = oracle.assign(C, 0.05)
+    exact = math.fsum(C[np.arange(500), r["row_to_col"]])
+    assert abs(r["cost"] - exact) <= 1e-15 * exact
+
+
+def test_float32_input_widened_exactly():
+    C = W.assignment_euclid_2d(50, 2).astype(np.float32)
+    r32 = oracle.assign(C, 0.05)
+    r64 = oracle.assign(C.astype(np.float64), 0.05)
+    assert np.array_equal(r32["row_to_col"], r64["row_to_col"])
+    assert r32["cost"] == r64["cost"]
