@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark: n = 10,000 assignment solve at eps = 0.01 on one GB300.
+
+Workload: A, B = 10,000 points each, i.i.d. uniform in [0,1]^2 (PCG64 seed 0),
+Euclidean cost divided by its maximum, FP64 (the paper's Sec. 5 synthetic
+experiment).  One step = one full pr_assign solve (rounding, every phase,
+completion, cost) with the cost matrix resident in HBM.  The 800 MB input and
+the 200 MB rounded matrix are both larger than L2, so no L2 flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+paper restated as plain C) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS_PER_SOLVE = 4  # k_init, k_quantise, k_phases, k_finish
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--eps", type=float, default=0.01)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"assignment n={a.n} eps={a.eps} (2-D uniform points, Euclidean cost / max, FP64)",
+            "n_rows": a.n, "n_cols": a.n, "eps": a.eps, "seed": a.seed,
+            "l2": "inputs larger than L2 (C 800 MB FP64, rounded costs 200 MB)"}
+
+
+METRIC = "n=10k assignment solve time at eps=0.01 (plain single solve)"
+
+
+def cpu_info():
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model, os.cpu_count()
+
+
+def time_oracle(C, eps, budget_s, max_runs=None):
+    """Time the unmodified oracle on the full workload: whole solves until the
+    budget is spent (at least one)."""
+    import oracle
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t0 = time.perf_counter()
+        oracle.assign(C, eps)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() >= t_end or (max_runs and len(times) >= max_runs):
+            break
+    return times
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2203_03732_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, earlier GB300 measurement)"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the phase kernel from the committed ncu
+    summary, or None when absent or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "k_phases_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("src_hash") != src_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from paper_2203_03732_gb300 import workloads as W
+    C = W.assignment_euclid_2d(a.n, a.seed)
+    for _ in range(max(0, a.warmup)):
+        time_oracle(C, a.eps, 0.0, max_runs=1)
+    times = []
+    for _ in range(a.steps):
+        times += time_oracle(C, a.eps, 0.0, max_runs=1)
+    ms = 1000.0 * sum(times) / len(times)
+    model, ncpu = cpu_info()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": workload_config(a),
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full solves of the workload, single thread, {model}, "
+                                   f"{ncpu} host cores present"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2203_03732_gb300 as prot
+    from paper_2203_03732_gb300 import _lib
+    from paper_2203_03732_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    L = _lib.load()
+
+    # Replicas only: every rank solves its own instance of the workload.
+    C_host = W.assignment_euclid_2d(a.n, a.seed)
+    C_pin = torch.from_numpy(C_host).pin_memory()
+    Cd = C_pin.to(dev)
+    ws = prot.Workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # One synchronous solve for the counters (deterministic: same every step).
+    ref = prot.assign(Cd, a.eps, ws=ws)
+    st = ref["stats"]
+    out = {k: v for k, v in ref.items() if k != "stats"}
+
+    for _ in range(a.warmup):
+        prot.assign(Cd, a.eps, ws=ws, sync=False, out=out)
+    torch.cuda.synchronize()
+
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(a.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(a.steps):
+        L.pr_set_kernel_events(ctypes.c_void_p(ev_k[i][0].cuda_event),
+                               ctypes.c_void_p(ev_k[i][1].cuda_event))
+        prot.assign(Cd, a.eps, ws=ws, sync=False, out=out)
+    L.pr_set_kernel_events(None, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    rc = L.pr_ws_status(ctypes.c_void_p(ws.buf.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    _lib.check(rc, "bench solve")
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    k_ms = [s.elapsed_time(t) for s, t in ev_k]
+    k_avg = sum(k_ms) / len(k_ms)
+    for k in ("row_to_col", "y_row", "y_col"):
+        assert torch.equal(out[k], ref[k]), "solve not reproducible"
+
+    # End to end: pinned host costs -> device, solve, matching + cost -> host.
+    r2c_host = torch.empty(a.n, dtype=torch.int32).pin_memory()
+    cost_host = torch.empty((), dtype=torch.float64).pin_memory()
+    Cd2 = torch.empty_like(Cd)
+    n_e2e = max(1, min(a.e2e_steps, a.steps))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(n_e2e):
+        Cd2.copy_(C_pin, non_blocking=True)
+        prot.assign(Cd2, a.eps, ws=ws, sync=False, out=out)
+        r2c_host.copy_(out["row_to_col"], non_blocking=True)
+        cost_host.copy_(out["cost"], non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / n_e2e
+    assert float(cost_host) == float(ref["cost"].cpu())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = measured_peak()
+    bytes_per_launch = float(st["bytes_scanned"])
+    achieved = bytes_per_launch / (k_avg * 1e-3) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        times = time_oracle(C_host, a.eps, a.cpu_seconds)
+        model, ncpu = cpu_info()
+        cpu = {"value": 1000.0 * sum(times) / len(times), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full solves of the same workload (single-threaded oracle, "
+                         f"~{a.cpu_seconds:.0f} s budget) on {model}, {ncpu} host cores present"}
+    line = {
+        "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic", "config": workload_config(a),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "kernel": "k_phases", "kernel_ms": k_avg,
+                     "bytes_per_launch": bytes_per_launch, "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Cd.numel() * 8),
+                "d2h_bytes_per_step": int(a.n * 4 + 8)},
+        "gpu_launches": KERNELS_PER_SOLVE * a.steps,
+        "clocks": clk,
+        "solver": {"phases": st["phases"], "rounds": st["rounds"], "rows_scanned": st["rows_scanned"],
+                   "free_at_stop": st["free_at_stop"], "threshold": st["threshold"],
+                   "cost": float(ref["cost"].cpu()), "phase_loop_ms": k_avg},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,124 @@
+/*
+ * prot.h -- C ABI of the GB300 push-relabel additive-approximation solver.
+ *
+ * Method: Lahn, Raghvendra, Zhang, "A Push-Relabel Based Additive
+ * Approximation for Optimal Transport" (arXiv 2203.03732).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers are DEVICE pointers unless a comment says "host".  The caller
+ *     owns every buffer; the library never allocates device memory.  Scratch
+ *     space is the caller's workspace `ws` of at least the bytes returned by
+ *     the matching *_workspace() query, 256-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it in order; nothing else is touched.
+ *   - Rows are the supply side B (the side whose free vertices propose, the
+ *     set B' of Sec. 2.2); columns are the demand side A.  Costs are row-major
+ *     with leading dimension `ldc` (elements).  The paper assumes the costs are
+ *     scaled so the largest is 1 (Sec. 1): every cost must be finite and in
+ *     [0, 1]; out-of-range costs make the call fail with PR_ERR_INVALID.
+ *   - Dual weights are returned as integers in units of eps (the paper keeps
+ *     every dual an integer multiple of eps, Sec. 2.2): y(v) = eps * y_int.
+ *   - Errors are returned as a status, never thrown.  A host-checked argument
+ *     error returns before anything is enqueued.  Errors found on the device
+ *     (cost out of range, barrier time-out, phase cap) are reported when the
+ *     call synchronises, which it does iff `stats` is non-NULL; otherwise
+ *     pr_ws_status() reads them later.  Outputs are unspecified on error.
+ *   - pr_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef PROT_H
+#define PROT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID = -1,         /* bad argument or cost outside [0,1]        */
+    PR_ERR_CUDA = -2,            /* a CUDA runtime call failed                */
+    PR_ERR_TIMEOUT = -3,         /* a device-side wait exceeded its budget    */
+    PR_ERR_NO_CONVERGENCE = -4,  /* phase cap reached (never for valid input) */
+    PR_ERR_WORKSPACE = -5,       /* workspace NULL, misaligned or too small   */
+    PR_ERR_CAPACITY = -6         /* an output buffer is too small             */
+} pr_status;
+
+typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_dtype;
+
+/* Counters of one solve (host struct). */
+typedef struct {
+    int64_t phases;        /* phases of Sec. 2.2 executed                       */
+    int64_t rounds;        /* rounds of step (I) in which a vertex proposed     */
+    int64_t bytes_scanned; /* bytes of rounded-cost rows read by the row scans  */
+    int64_t rows_scanned;  /* row scans started (one per free vertex per round) */
+    int32_t free_at_stop;  /* |B'| when the loop stopped (<= threshold)         */
+    int32_t threshold;     /* T = floor(eps * n_rows)                           */
+} pr_stats;
+
+/*
+ * Workspace bytes pr_assign needs for an n_rows x n_cols problem
+ * (0 if the sizes are invalid).
+ */
+size_t pr_assign_workspace(int32_t n_rows, int32_t n_cols);
+
+/*
+ * pr_assign -- additive approximation of the assignment problem.
+ *
+ * Defines: Sec. 1 (problem statement; c(M) is the sum of matched costs),
+ * Eq. (1) (rounding cbar = eps*floor(c/eps)), Sec. 2.2 (phases: greedy
+ * maximal matching on admissible edges, push/evict, dual update; stop when at
+ * most eps*|B| vertices of B are free, then match the rest arbitrarily),
+ * Sec. 3.3 (unbalanced case |B| <= |A|).  The result's cost is within
+ * 3*eps*n_rows of the optimum (Sec. 2.1, Lemma 3.1).
+ *
+ * The maximal matching of each phase is the deterministic round rule: every
+ * still-active free row proposes to its lowest-index admissible column not
+ * taken in an earlier round of the phase, each column accepts its
+ * lowest-index proposer, rounds repeat until no row proposes.  Completion
+ * matches the k-th free row (ascending) with the k-th free column
+ * (ascending); duals are left as the main routine ended.
+ *
+ *   C          n_rows x n_cols costs, dtype dt, leading dimension ldc >= n_cols
+ *   eps        0 < eps < 1 with floor(1/eps) <= 32766
+ *   n_rows     1 <= n_rows <= n_cols <= 2^24
+ *   row_to_col [n_rows] out: column matched to each row (always >= 0)
+ *   col_to_row [n_cols] out: row matched to each column, -1 if none
+ *   y_row      [n_rows] out: integer duals of the rows (>= 1), units of eps
+ *   y_col      [n_cols] out: integer duals of the columns (<= 0), units of eps
+ *   cost       [1] out: FP64 sum_i C[i, row_to_col[i]] in input units
+ *   stats      host, may be NULL; non-NULL makes the call synchronous
+ *   ws, ws_bytes  device workspace, >= pr_assign_workspace(n_rows, n_cols)
+ */
+pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int32_t n_cols,
+                    double eps, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                    int32_t *y_col, double *cost, pr_stats *stats, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/*
+ * Synchronise `stream` and return the device-side status recorded in a
+ * workspace by the last call that used it (PR_OK if none).  For callers that
+ * pass stats == NULL.  `ws` must be a workspace of that call.
+ */
+pr_status pr_ws_status(const void *ws, void *stream);
+
+/*
+ * Profiling hook (thread-local).  When `start` and `stop` are cudaEvent_t
+ * handles, each later solver call made by this thread records `start` right
+ * before and `stop` right after its dominant kernel (the persistent phase
+ * kernel) on the call's stream, so a caller can time that kernel alone with
+ * CUDA events.  Pass NULL, NULL to stop.  The events are borrowed, not owned.
+ */
+void pr_set_kernel_events(void *start, void *stop);
+
+/* Thread-local text of the last error (never NULL). */
+const char *pr_last_error(void);
+
+/* Name of a status code. */
+const char *pr_status_string(pr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROT_H */

@@ -1,0 +1,89 @@
+"""ctypes binding of ``libprot.so`` (the C ABI declared in ``include/prot.h``).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+There is no CPU fallback; if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_PKG, "libprot.so")
+
+PR_OK = 0
+PR_ERR_INVALID = -1
+PR_ERR_CUDA = -2
+PR_ERR_TIMEOUT = -3
+PR_ERR_NO_CONVERGENCE = -4
+PR_ERR_WORKSPACE = -5
+PR_ERR_CAPACITY = -6
+PR_F32 = 0
+PR_F64 = 1
+
+
+class PrStats(ctypes.Structure):
+    _fields_ = [
+        ("phases", ctypes.c_int64),
+        ("rounds", ctypes.c_int64),
+        ("bytes_scanned", ctypes.c_int64),
+        ("rows_scanned", ctypes.c_int64),
+        ("free_at_stop", ctypes.c_int32),
+        ("threshold", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); every symbol include/prot.h declares.
+SIGNATURES = {
+    "pr_assign_workspace": (_sz, [_i32, _i32]),
+    "pr_assign": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp,
+                                 ctypes.POINTER(PrStats), _vp, _sz, _vp]),
+    "pr_ws_status": (ctypes.c_int, [_vp, _vp]),
+    "pr_set_kernel_events": (None, [_vp, _vp]),
+    "pr_last_error": (ctypes.c_char_p, []),
+    "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load(path: str = SO_PATH):
+    """Load the CUDA library; raises if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                if hasattr(L, name):
+                    fn = getattr(L, name)
+                    fn.restype = res
+                    fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str):
+    if status != PR_OK:
+        msg = load().pr_last_error().decode(errors="replace")
+        raise PrError(status, f"{what}: {msg}")

@@ -1,0 +1,84 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports
+every function include/prot.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(pr_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2203_03732_gb300 import build
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("pr_assign", "pr_assign_workspace", "pr_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header(libpath):
+    from paper_2203_03732_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_workspace_query_without_gpu(libpath):
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load(libpath)
+    assert L.pr_assign_workspace(0, 10) == 0
+    assert L.pr_assign_workspace(11, 10) == 0
+    w = L.pr_assign_workspace(10000, 10000)
+    assert w >= 10000 * 10000 * 2 and w % 256 == 0
+    assert L.pr_status_string(-3) == b"PR_ERR_TIMEOUT"
+
+
+def test_host_argument_errors_without_gpu(libpath):
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load(libpath)
+    st = _lib.PrStats()
+    rc = L.pr_assign(None, 1, 10, 10, 10, 0.1, None, None, None, None, None, ctypes.byref(st),
+                     None, 0, None)
+    assert rc == _lib.PR_ERR_INVALID
+    assert b"NULL" in L.pr_last_error()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2203_03732_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(ImportError):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
+
+
+def test_no_oracle_import_in_product_path():
+    pkg = os.path.join(ROOT, "paper_2203_03732_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "prot_oracle" not in txt, f

@@ -1,0 +1,209 @@
+"""GPU parity of pr_assign against the CPU oracle (bit-exact matching, both
+dual vectors and the phase/round counts; FP64 cost within 1e-12 relative).
+
+Sizes span one chunk, several chunks and ragged tails of the row scan
+(4096-column chunks, 8-column vectors), the unbalanced case, FP32 input,
+closed-form special cases, and the full n = 10,000 workloads.
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_03732_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def prot():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_03732_gb300 import build
+    build.build()
+    import paper_2203_03732_gb300 as P
+    return P
+
+
+def gpu_solve(P, C, eps):
+    import torch
+    r = P.assign(torch.from_numpy(C).cuda(), eps)
+    out = {k: r[k].cpu().numpy() for k in ("row_to_col", "col_to_row", "y_row", "y_col")}
+    out["cost"] = float(r["cost"].cpu())
+    out["stats"] = r["stats"]
+    return out
+
+
+def assert_parity(got, ref):
+    for k in ("row_to_col", "col_to_row", "y_row", "y_col"):
+        assert np.array_equal(got[k], ref[k]), f"{k} differs"
+    assert got["stats"]["phases"] == ref["stats"]["phases"]
+    assert got["stats"]["rounds"] == ref["stats"]["rounds"]
+    assert got["stats"]["free_at_stop"] == ref["stats"]["free_at_stop"]
+    assert got["stats"]["threshold"] == ref["threshold"]
+    assert abs(got["cost"] - ref["cost"]) <= COST_RTOL * max(abs(ref["cost"]), 1e-300)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_config_n1000_sq_euclid(prot, seed):
+    C = W.assignment_sq_euclid_2d(1000, seed)
+    assert_parity(gpu_solve(prot, C, 0.1), oracle.assign(C, 0.1))
+
+
+@pytest.mark.parametrize("n", [7, 64, 257, 1000, 2049, 4097, 5003])
+@pytest.mark.parametrize("eps", [0.1, 0.01, 0.005])
+def test_sizes_and_eps(prot, n, eps):
+    C = W.assignment_euclid_2d(n, 11 + n)
+    assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+@pytest.mark.parametrize("nB,nA", [(100, 173), (1000, 4100), (1, 9), (33, 8200)])
+def test_unbalanced(prot, nB, nA):
+    C = W.assignment_euclid_2d(nB, 3, n_a=nA)
+    for eps in (0.1, 0.02):
+        assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+def test_float32_input(prot):
+    C = W.assignment_euclid_2d(1500, 4).astype(np.float32)
+    assert_parity(gpu_solve(prot, C, 0.01), oracle.assign(C, 0.01))
+
+
+def test_leading_dimension(prot):
+    import torch
+    C = W.assignment_euclid_2d(600, 5)
+    big = np.zeros((600, 640))
+    big[:, :600] = C
+    Ct = torch.from_numpy(big).cuda()[:, :600]
+    assert Ct.stride(0) == 640
+    r = prot.assign(Ct, 0.01)
+    ref = oracle.assign(C, 0.01)
+    assert np.array_equal(r["row_to_col"].cpu().numpy(), ref["row_to_col"])
+    assert np.array_equal(r["y_row"].cpu().numpy(), ref["y_row"])
+
+
+@pytest.mark.parametrize("n,k,eps", [(300, 0.55, 0.1), (129, 1.0, 0.25), (1, 0.73, 0.001)])
+def test_constant_costs(prot, n, k, eps):
+    C = np.full((n, n), k)
+    got, ref = gpu_solve(prot, C, eps), oracle.assign(C, eps)
+    assert_parity(got, ref)
+    assert got["row_to_col"].tolist() == list(range(n))
+
+
+def test_zero_diagonal_and_permutation(prot):
+    n = 4500
+    C = 1.0 - np.eye(n)
+    got = gpu_solve(prot, C, 0.1)
+    assert got["row_to_col"].tolist() == list(range(n))
+    assert got["stats"]["phases"] == 1 and got["stats"]["rounds"] == 1
+    pi = np.random.default_rng(0).permutation(n)
+    C = np.ones((n, n))
+    C[np.arange(n), pi] = 0.0
+    got = gpu_solve(prot, C, 0.2)
+    assert got["row_to_col"].tolist() == pi.tolist()
+
+
+def test_smallest_eps(prot):
+    """floor(1/eps) = 32766, the largest the 16-bit keys allow."""
+    eps = 1.0 / 32766.5
+    C = W.assignment_euclid_2d(40, 9)
+    assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.01, 0.005])
+def test_full_size_n10000(prot, eps):
+    """The n = 10,000 Euclidean workload in the launch configuration the
+    bench times, compared in full with the oracle."""
+    C = W.assignment_euclid_2d(10000, 0)
+    assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+def test_repeat_is_deterministic(prot):
+    C = W.assignment_euclid_2d(3000, 21)
+    a = gpu_solve(prot, C, 0.01)
+    b = gpu_solve(prot, C, 0.01)
+    for k in ("row_to_col", "y_row", "y_col"):
+        assert np.array_equal(a[k], b[k])
+    assert a["cost"] == b["cost"]
+
+
+# ---------------------------------------------------------------------------
+# Error paths (host-side checks and device-side status; nothing faults)
+# ---------------------------------------------------------------------------
+
+def test_cost_out_of_range_reported(prot):
+    import torch
+    C = W.assignment_euclid_2d(100, 1)
+    C[37, 5] = 1.5
+    with pytest.raises(prot.PrError) as e:
+        prot.assign(torch.from_numpy(C).cuda(), 0.1)
+    assert e.value.status == -1
+    C[37, 5] = np.nan
+    with pytest.raises(prot.PrError):
+        prot.assign(torch.from_numpy(C).cuda(), 0.1)
+
+
+def test_bad_arguments(prot):
+    import torch
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load()
+    C = torch.rand(10, 20, dtype=torch.float64, device="cuda")
+    for eps in (0.0, 1.0, -0.1, 1e-6):
+        with pytest.raises(prot.PrError):
+            prot.assign(C, eps)
+    with pytest.raises(ValueError):
+        prot.assign(C.t().contiguous(), 0.1)  # n_rows > n_cols
+    # workspace too small / misaligned
+    out = [torch.empty(10, dtype=torch.int32, device="cuda") for _ in range(2)]
+    outa = [torch.empty(20, dtype=torch.int32, device="cuda") for _ in range(2)]
+    cost = torch.empty((), dtype=torch.float64, device="cuda")
+    ws = torch.empty(L.pr_assign_workspace(10, 20), dtype=torch.uint8, device="cuda")
+    st = _lib.PrStats()
+    rc = L.pr_assign(C.data_ptr(), 1, 20, 10, 20, 0.1, out[0].data_ptr(), outa[0].data_ptr(),
+                     out[1].data_ptr(), outa[1].data_ptr(), cost.data_ptr(), ctypes.byref(st),
+                     ws.data_ptr(), ws.numel() - 1, None)
+    assert rc == _lib.PR_ERR_WORKSPACE
+    rc = L.pr_assign(C.data_ptr(), 1, 20, 10, 20, 0.1, out[0].data_ptr(), outa[0].data_ptr(),
+                     out[1].data_ptr(), outa[1].data_ptr(), cost.data_ptr(), ctypes.byref(st),
+                     ws.data_ptr() + 8, ws.numel() - 8, None)
+    assert rc == _lib.PR_ERR_WORKSPACE
+    rc = L.pr_assign(C.data_ptr(), 1, 19, 10, 20, 0.1, out[0].data_ptr(), outa[0].data_ptr(),
+                     out[1].data_ptr(), outa[1].data_ptr(), cost.data_ptr(), ctypes.byref(st),
+                     ws.data_ptr(), ws.numel(), None)
+    assert rc == _lib.PR_ERR_INVALID
+    assert b"ldc" in L.pr_last_error()
+
+
+def test_barrier_timeout_reported_not_hung(prot, monkeypatch):
+    """A one-cycle spin budget makes every waiting CTA give up at its first
+    grid barrier: the call returns PR_ERR_TIMEOUT and the context stays
+    usable (the next solve is exact)."""
+    import torch
+    C = W.assignment_euclid_2d(2000, 2)
+    monkeypatch.setenv("PR_SPIN_LIMIT_CYCLES", "1")
+    with pytest.raises(prot.PrError) as e:
+        prot.assign(torch.from_numpy(C).cuda(), 0.01)
+    assert e.value.status == -3
+    monkeypatch.delenv("PR_SPIN_LIMIT_CYCLES")
+    assert_parity(gpu_solve(prot, C, 0.01), oracle.assign(C, 0.01))
+
+
+def test_async_status_query(prot):
+    import torch
+    from paper_2203_03732_gb300 import _lib
+    C = W.assignment_euclid_2d(200, 1)
+    C[3, 3] = -0.5
+    ws = prot.Workspace("cuda")
+    with pytest.raises(prot.PrError):
+        prot.assign(torch.from_numpy(C).cuda(), 0.1, ws=ws)
+    C[3, 3] = 0.5
+    r = prot.assign(torch.from_numpy(C).cuda(), 0.1, ws=ws, sync=False)
+    rc = _lib.load().pr_ws_status(ctypes.c_void_p(ws.buf.data_ptr()), None)
+    assert rc == 0
+    ref = oracle.assign(C, 0.1)
+    assert np.array_equal(r["row_to_col"].cpu().numpy(), ref["row_to_col"])
