@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     return ap.parse_args()
 
 
@@ -194,6 +195,27 @@ def run_reference(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_e2e(a, torch, prot, C_pin, Cd, ws, out, stream, ref):
+    r2c_host = torch.empty(a.n, dtype=torch.int32).pin_memory()
+    cost_host = torch.empty((), dtype=torch.float64).pin_memory()
+    Cd2 = torch.empty_like(Cd)
+    n_e2e = max(1, min(a.e2e_steps, a.steps))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(n_e2e):
+        Cd2.copy_(C_pin, non_blocking=True)
+        prot.assign(Cd2, a.eps, ws=ws, sync=False, out=out)
+        r2c_host.copy_(out["row_to_col"], non_blocking=True)
+        cost_host.copy_(out["cost"], non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / n_e2e
+    assert float(cost_host) == float(ref["cost"].cpu())
+    return {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Cd.numel() * 8),
+            "d2h_bytes_per_step": int(a.n * 4 + 8)}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -235,6 +257,9 @@ def main():
 
     ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(a.steps)]
+    for s0, s1 in ev_k:  # torch creates the event handles on first record
+        s0.record(stream)
+        s1.record(stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -266,22 +291,9 @@ def main():
         assert torch.equal(out[k], ref[k]), "solve not reproducible"
 
     # End to end: pinned host costs -> device, solve, matching + cost -> host.
-    r2c_host = torch.empty(a.n, dtype=torch.int32).pin_memory()
-    cost_host = torch.empty((), dtype=torch.float64).pin_memory()
-    Cd2 = torch.empty_like(Cd)
-    n_e2e = max(1, min(a.e2e_steps, a.steps))
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(n_e2e):
-        Cd2.copy_(C_pin, non_blocking=True)
-        prot.assign(Cd2, a.eps, ws=ws, sync=False, out=out)
-        r2c_host.copy_(out["row_to_col"], non_blocking=True)
-        cost_host.copy_(out["cost"], non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / n_e2e
-    assert float(cost_host) == float(ref["cost"].cpu())
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(a, torch, prot, C_pin, Cd, ws, out, stream, ref)
 
     if rank != 0:
         if dist:
@@ -308,8 +320,7 @@ def main():
                      "kernel": "k_phases", "kernel_ms": k_avg,
                      "bytes_per_launch": bytes_per_launch, "peak_source": peak_src},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Cd.numel() * 8),
-                "d2h_bytes_per_step": int(a.n * 4 + 8)},
+        "e2e": e2e,
         "gpu_launches": KERNELS_PER_SOLVE * a.steps,
         "clocks": clk,
         "solver": {"phases": st["phases"], "rounds": st["rounds"], "rows_scanned": st["rows_scanned"],
