@@ -11,7 +11,7 @@
  *
  * Units: every dual weight and rounded cost is kept as an integer multiple of
  * eps (Sec. 2.1 says all duals stay integer multiples of eps), so
- *   cb(b,a) = floor(c(b,a) / eps)            (Eq. 1, divided by eps)
+ *   cb(b,a) = floor(c(b,a) / eps), exact quotient (Eq. 1, divided by eps)
  *   admissible(a,b)  <=>  y(a) + y(b) == cb + 1   (slack 0, Sec. 2.1 / Eq. 2)
  *   matched edge     <=>  y(a) + y(b) == cb       (Eq. 3)
  * Rows are the vertices of B (the supply side whose free vertices form B'),
@@ -45,9 +45,22 @@
 /* Eq. (1): rounding of costs to integer multiples of eps.                   */
 /* ------------------------------------------------------------------------ */
 
-/* cb = floor(C / eps) with an IEEE FP64 divide.  Costs must be finite and in
- * [0, 1] (Sec. 1 assumes the costs are scaled so that the largest is 1).
- * Returns 0, or -1 at the first invalid cost. */
+/* Eq. (1) in eps units: cb = floor(c / eps) of the EXACT real quotient of
+ * the two given FP64 numbers, i.e. the largest integer k with k * eps <= c.
+ * The comparison k * eps <= c is decided exactly: fma(-k, eps, c) forms
+ * c - k*eps exactly and rounds once, which keeps its sign (no underflow can
+ * occur for k >= 1 since eps > 3e-5).  A rounded division gives a start value
+ * within one of the answer.  Costs must be finite and in [0, 1] (Sec. 1
+ * assumes the costs are scaled so that the largest is 1). */
+static int32_t exact_floor_div(double c, double eps)
+{
+    int32_t k = (int32_t)floor(c / eps);
+    while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
+    while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
+    return k;
+}
+
+/* Returns 0, or -1 at the first invalid cost. */
 int or_quantise_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA,
                     double eps, int32_t *cb)
 {
@@ -55,7 +68,7 @@ int or_quantise_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA,
         for (int32_t a = 0; a < nA; ++a) {
             double c = C[(int64_t)b * ldc + a];
             if (!(c >= 0.0 && c <= 1.0)) return -1;
-            cb[(int64_t)b * nA + a] = (int32_t)floor(c / eps);
+            cb[(int64_t)b * nA + a] = exact_floor_div(c, eps);
         }
     }
     return 0;
@@ -69,7 +82,7 @@ int or_quantise_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA,
         for (int32_t a = 0; a < nA; ++a) {
             double c = (double)C[(int64_t)b * ldc + a];
             if (!(c >= 0.0 && c <= 1.0)) return -1;
-            cb[(int64_t)b * nA + a] = (int32_t)floor(c / eps);
+            cb[(int64_t)b * nA + a] = exact_floor_div(c, eps);
         }
     }
     return 0;

@@ -73,23 +73,47 @@ def test_quantise_hand_values():
     cb = oracle.quantise(C, 0.25)
     assert cb.tolist() == [[0, 4, 2, 1], [1, 3, 0, 0]]
     cb = oracle.quantise(C, 0.1)
-    # 1/0.1, 0.5/0.1, 0.1/0.1 all round to exact integers in FP64.
-    assert cb.tolist() == [[0, 10, 5, 2], [2, 7, 0, 1]]
+    # the FP64 number 0.1 is slightly above 1/10, so 10 * 0.1 > 1.0 exactly:
+    # floor(1.0 / 0.1) = 9 (exact quotient 9.99...), likewise 0.5 -> 4.
+    assert cb.tolist() == [[0, 9, 4, 2], [2, 7, 0, 1]]
 
 
-def test_quantise_matches_exact_floor_off_boundary():
-    """cb = floor(c/eps) exactly (rational arithmetic) wherever c/eps is not
-    within one rounding of an integer."""
+def exact_floor(c, eps):
+    return math.floor(Fraction(c) / Fraction(eps))
+
+
+def test_quantise_is_exact_floor_everywhere():
+    """Eq. (1) exactly: cb = floor of the exact rational quotient c/eps, for
+    random costs and for costs placed on and next to multiples of eps."""
     g = np.random.default_rng(7)
-    C = g.random((20, 30))
-    for eps in (0.1, 0.01, 0.005, 0.3):
+    for eps in (0.1, 0.01, 0.005, 0.3, 1.0 / 3.0, 1.0 / 32766.5):
+        K = int(math.floor(1.0 / eps))
+        vals = list(g.random(400))
+        ks = g.integers(0, K + 1, size=200)
+        for k in ks:
+            v = float(k) * eps                   # RN(k * eps): either side of k*eps
+            for x in (v, np.nextafter(v, 0.0), np.nextafter(v, 2.0)):
+                if 0.0 <= x <= 1.0:
+                    vals.append(float(x))
+        vals += [0.0, 1.0, 5e-324, np.nextafter(1.0, 0.0)]
+        C = np.array(vals, dtype=np.float64).reshape(1, -1)
         cb = oracle.quantise(C, eps)
-        for b in range(C.shape[0]):
-            for a in range(C.shape[1]):
-                q = Fraction(C[b, a]) / Fraction(eps)
-                fl = math.floor(q)
-                if q - fl > Fraction(1, 10**9) and (fl + 1) - q > Fraction(1, 10**9):
-                    assert cb[b, a] == fl
+        want = [exact_floor(c, eps) for c in C[0]]
+        assert cb[0].tolist() == want
+
+
+def test_quantise_exact_floor_differs_from_rounded_division():
+    """There are costs where floor(RN(c/eps)) overshoots the exact floor; the
+    oracle follows Eq. (1) exactly there."""
+    eps = 0.1
+    hits = 0
+    for k in range(1, 11):
+        for x in (float(k) * eps, np.nextafter(float(k) * eps, 0.0)):
+            if x <= 1.0 and math.floor(x / eps) != exact_floor(x, eps):
+                hits += 1
+                cb = oracle.quantise(np.array([[x]]), eps)
+                assert cb[0, 0] == exact_floor(x, eps)
+    assert hits > 0
 
 
 def test_quantise_rejects_out_of_range():
