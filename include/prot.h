@@ -42,7 +42,8 @@ typedef enum {
     PR_ERR_TIMEOUT = -3,         /* a device-side wait exceeded its budget    */
     PR_ERR_NO_CONVERGENCE = -4,  /* phase cap reached (never for valid input) */
     PR_ERR_WORKSPACE = -5,       /* workspace NULL, misaligned or too small   */
-    PR_ERR_CAPACITY = -6         /* an output buffer is too small             */
+    PR_ERR_CAPACITY = -6,        /* an output buffer is too small             */
+    PR_ERR_INTERNAL = -7         /* a device-side consistency check failed    */
 } pr_status;
 
 typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_dtype;

@@ -19,6 +19,7 @@ PR_ERR_TIMEOUT = -3
 PR_ERR_NO_CONVERGENCE = -4
 PR_ERR_WORKSPACE = -5
 PR_ERR_CAPACITY = -6
+PR_ERR_INTERNAL = -7
 PR_F32 = 0
 PR_F64 = 1
 

@@ -87,6 +87,7 @@ extern "C" const char *pr_status_string(pr_status s) {
         case PR_ERR_NO_CONVERGENCE: return "PR_ERR_NO_CONVERGENCE";
         case PR_ERR_WORKSPACE: return "PR_ERR_WORKSPACE";
         case PR_ERR_CAPACITY: return "PR_ERR_CAPACITY";
+        case PR_ERR_INTERNAL: return "PR_ERR_INTERNAL";
     }
     return "PR_UNKNOWN";
 }

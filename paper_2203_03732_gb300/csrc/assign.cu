@@ -1,16 +1,27 @@
 // assign.cu -- pr_assign: the push-relabel assignment solver on one GB300.
 //
 // Pipeline (all on the caller's stream, no host round trip inside a solve):
-//   k_init      y(b) = 1, y(a) = 0, M empty, B' = all rows        (Sec. 2.2)
-//   k_quantise  cbar = floor(c / eps) as uint16, row-major [b][a] (Eq. 1)
-//   k_phases    persistent cooperative kernel: all phases, all rounds
-//   k_finish    completion + FP64 cost + y(A) output             (Sec. 2.1)
+//   k_init      y(b) = 1, y(a) = 0, M empty                        (Sec. 2.2)
+//   k_quantise  cbar = floor(c / eps) exactly, uint16, [b][a]      (Eq. 1)
+//   k_phases    persistent cooperative kernel: every phase and round
+//   k_decode    matching and y(A) out of the per-column words
+//   k_finish    completion + FP64 cost                             (Sec. 2.1)
 //
-// Integer form (units of eps): with k(a) = -y(a) >= 0, an edge is admissible
+// Integer form (units of eps): with k(a) = -y(a) >= 0 an edge is admissible
 // (slack 0, Eq. 2 with equality) iff  cbar(b,a) + k(a) == y(b) - 1.  Both
-// cbar and k fit 16 bits (Lemma 3.2 bounds |y| by floor(1/eps) + 2), so a
-// 16-byte load of eight cbar values is tested against eight k values with
-// four 32-bit adds: two 16-bit lanes per word, no carry between them.
+// cbar and k fit 16 bits (Lemma 3.2 bounds |y| by floor(1/eps) + 2), so one
+// 16-byte load of eight cbar values meets eight k values in four 32-bit adds
+// (two 16-bit lanes per word, no carry between them).
+//
+// One 64-bit word per column carries all of step (I) and the matching:
+//   word(a) = (R << 32) | (0xFFFFFFFF - b)
+// where R is a global round counter (never reset) and b the proposer.  Every
+// proposal is an atomicMax, so within a round the lowest b wins, and a later
+// phase overwrites an earlier one.  A column is "taken" in the current phase
+// iff its tag lies in [first round of the phase, current round).  The word of
+// a column last won in an earlier phase names its current partner, so the
+// first proposer of a phase learns from atomicMax's return value both that
+// it is first and which row step (II) evicts.  Nothing is ever reset.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,21 +32,21 @@
 namespace prot {
 namespace {
 
-constexpr int kThreads = 512;           // threads per CTA of the phase kernel
+constexpr int kThreads = 512;             // threads per CTA of the phase kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kUnroll = 8;              // 16-byte loads in flight per lane per chunk
+constexpr int kUnroll = 8;                // 16-byte loads in flight per lane per chunk
 constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk (4 KiB)
-constexpr int kQueue = 1024;            // per-CTA job queue / append buffer capacity
-constexpr unsigned long long kEmpty = ~0ull;
-constexpr uint16_t kPadCost = 0x7FFF;   // cbar of padding columns
-constexpr uint16_t kPadKey = 0x8000;    // k of padding columns: pad sum 0xFFFF never matches
+constexpr int kListSm = 2048;             // list entries kept in shared memory
+constexpr int kBatch = 256;               // items turned into scan jobs at a time
+constexpr uint16_t kPadCost = 0x7FFF;     // cbar of padding columns
+constexpr uint16_t kPadKey = 0x8000;      // k of padding columns: pad sum 0xFFFF never matches
+constexpr int kMaxGrid = 1023;            // barrier payload field width
 
 // Control block at the start of the workspace.
 struct Ctl {
     WsHead head;
-    int nfree[3];        // |B'| lists, ring by phase index
-    int nprop[3];        // proposer lists, ring by global step index
-    int nwon[2];         // columns won in a phase (prop reset / key update), by phase parity
+    unsigned long long bar_acc;  // barrier arrivals + payload (see grid_sync)
+    unsigned long long bar_pub;  // (generation << 32) | published payload
     int free_at_stop;
     int pad0;
     long long phases;
@@ -45,22 +56,24 @@ struct Ctl {
 };
 
 struct Layout {
-    size_t ctl, cb, ka, ptr, prop, freel, propl, wonl, total;
+    size_t ctl, cb, ka, prop, lists, total;
     int ldq;
+    size_t list_stride;  // ints per CTA in the list region
 };
 
-Layout make_layout(int nB, int nA) {
+// Per-CTA overflow storage: two row lists (this phase, next phase) and two
+// proposal lists of (b, a) pairs (this round, previous round), each able to
+// hold every row.
+Layout make_layout(int nB, int nA, int grid) {
     Layout L;
     Carver c;
     L.ldq = (nA + 7) & ~7;
     L.ctl = c.take<Ctl>(1);
     L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
     L.ka = c.take<uint16_t>(L.ldq);
-    L.ptr = c.take<int>(nB);
-    L.prop = c.take<unsigned long long>(2 * (size_t)nA);
-    L.freel = c.take<int>(3 * (size_t)nB);
-    L.propl = c.take<int>(3 * (size_t)nB);
-    L.wonl = c.take<int>(2 * (size_t)nB);
+    L.prop = c.take<unsigned long long>((size_t)nA);
+    L.list_stride = 6 * (size_t)nB;
+    L.lists = c.take<int>((size_t)grid * L.list_stride);
     L.total = c.total();
     return L;
 }
@@ -70,52 +83,64 @@ struct Params {
     const uint16_t *cb;
     uint16_t *ka;
     int *y_b;
-    int *match_b;
-    int *match_a;
-    int *ptr;
-    unsigned long long *prop;  // [2][nA]
-    int *freel;                // [3][nB]
-    int *propl;                // [3][nB]
-    int *wonl;                 // [2][nB]
+    unsigned long long *prop;
+    int *lists;
+    size_t list_stride;
     int nB, nA, ldq, T;
     long long phase_cap;
     long long spin_limit;
 };
 
+__device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
+__device__ __forceinline__ int row_of(unsigned long long w) { return (int)(0xFFFFFFFFu - (unsigned)w); }
+__device__ __forceinline__ unsigned long long word_of(unsigned R, int b) {
+    return ((unsigned long long)R << 32) | (0xFFFFFFFFu - (unsigned)b);
+}
+
 // ---------------------------------------------------------------------------
 // k_init
 // ---------------------------------------------------------------------------
-__global__ void k_init(Params p) {
+__global__ void k_init(Params p, int *match_b) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (int b = t0; b < p.nB; b += stride) {
         p.y_b[b] = 1;
-        p.match_b[b] = -1;
-        p.freel[b] = b;  // B' of phase 0 = every row
+        match_b[b] = -1;
     }
     for (int a = t0; a < p.ldq; a += stride) {
         p.ka[a] = a < p.nA ? 0 : kPadKey;
-        if (a < p.nA) {
-            p.match_a[a] = -1;
-            p.prop[a] = kEmpty;
-            p.prop[(size_t)p.nA + a] = kEmpty;
-        }
+        if (a < p.nA) p.prop[a] = word_of(0, -1);  // round 0, no partner
     }
     if (t0 == 0) {
         Ctl *c = p.ctl;
         memset(c, 0, sizeof(Ctl));
         c->head.magic = kWsMagic;
-        c->nfree[0] = p.nB;
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_quantise: cbar = floor(c / eps) with an IEEE FP64 divide (Eq. 1).  One
-// thread per 8 consecutive columns of a row; one 16-byte store.
+// k_quantise: Eq. (1) exactly, cbar = largest k with k * eps <= c.
+// An FP32 estimate q of c/eps is within 0.006 of the exact quotient (three
+// roundings of relative size 2^-24 on a quotient <= 32767), so floor(q) is
+// exact whenever q is at least 1/64 away from an integer.  Otherwise the
+// integer is settled with fma(-k, eps, c), whose sign is that of the exact
+// c - k*eps.  No FP64 division runs per element.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t quantise_one(double c, double eps, float inv_eps) {
+    const float q = __fmul_rn((float)c, inv_eps);
+    const float kf = floorf(q);
+    const float fr = q - kf;
+    int k = (int)kf;
+    if (!(fr >= 0.015625f && fr <= 0.984375f)) {
+        while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
+        while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
+    }
+    return (uint32_t)k;
+}
+
 template <class T>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
-                           double eps, uint16_t *__restrict__ cb, WsHead *head) {
+                           double eps, float inv_eps, uint16_t *__restrict__ cb, WsHead *head) {
     const int groups = ldq >> 3;
     const long long total = (long long)nB * groups;
     bool bad = false;
@@ -137,7 +162,7 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
                         bad = true;
                         h[k] = 0;
                     } else {
-                        h[k] = (uint32_t)floor(__ddiv_rn(c, eps));
+                        h[k] = quantise_one(c, eps, inv_eps);
                     }
                 } else {
                     h[k] = kPadCost;
@@ -151,13 +176,32 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
 }
 
 // ---------------------------------------------------------------------------
-// Row scan: the lowest column a >= start with cbar(b,a) + k(a) == tgt that no
-// earlier round of this phase took.  A warp scans one chunk of kChunk columns
-// with kUnroll independent 16-byte loads per lane in flight.
+// Row scan.  For the phase-start keys k0, the edge (a,b) is admissible iff
+// cbar + k0(a) == tgt.  The keys read here may already carry the +1 of a
+// column first proposed to in the current round (the +1 of an earlier round
+// of the phase is always visible: a grid barrier separates them), and
+// feasibility (I2) gives cbar + k0 >= tgt for a free row.  Hence:
+//   seen == tgt     -> admissible and not taken: a candidate;
+//   seen == tgt + 1 -> admissible iff a was proposed to in this phase, and a
+//                      candidate iff that happened in this very round R.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned match_mask(uint4 c, uint4 k, uint32_t tgt2) {
-    const uint32_t w0 = (c.x + k.x) ^ tgt2, w1 = (c.y + k.y) ^ tgt2;
-    const uint32_t w2 = (c.z + k.z) ^ tgt2, w3 = (c.w + k.w) ^ tgt2;
+__device__ __forceinline__ uint4 ld_cg_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_nc_na_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
+    const uint32_t w0 = s.x ^ t2, w1 = s.y ^ t2, w2 = s.z ^ t2, w3 = s.w ^ t2;
     unsigned m = 0;
     m |= (w0 & 0xFFFFu) == 0 ? 1u : 0u;
     m |= (w0 >> 16) == 0 ? 2u : 0u;
@@ -170,47 +214,59 @@ __device__ __forceinline__ unsigned match_mask(uint4 c, uint4 k, uint32_t tgt2) 
     return m;
 }
 
-// Returns the column found, or -1.  `ks` points at the phase's key copy
-// (shared memory).  Round tags: a column is taken iff its proposal word
-// carries a round tag < r.
-__device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
-                                               const uint16_t *ks, int c0, int start, int ldq,
-                                               uint32_t tgt2,
-                                               const unsigned long long *prop, unsigned r,
+// Lowest candidate column in [c0, c0 + kChunk) that is >= start, or -1.
+__device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ka,
+                                               int c0, int start, int ldq, uint32_t tgt,
+                                               const unsigned long long *prop, unsigned R,
                                                int lane) {
-    uint4 cv[kUnroll], kv[kUnroll];
+    uint4 sv[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int idx = c0 + u * 256 + lane * 8;
         if (idx < ldq) {
-            cv[u] = ld_nc_v4(row + idx);
-            kv[u] = *reinterpret_cast<const uint4 *>(ks + idx);
+            const uint4 c = ld_nc_na_v4(row + idx);
+            const uint4 k = ld_cg_v4(ka + idx);
+            sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
         } else {
-            cv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-            kv[u] = make_uint4(0, 0, 0, 0);
+            sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         }
     }
+    const uint32_t t2 = tgt | (tgt << 16);
+    const uint32_t t2p = (tgt + 1) | ((tgt + 1) << 16);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int idx = c0 + u * 256 + lane * 8;
-        unsigned m = match_mask(cv[u], kv[u], tgt2);
+        unsigned sure = eq_mask(sv[u], t2);
+        unsigned amb = eq_mask(sv[u], t2p);
         const int lo = start - idx;
-        if (lo > 0) m = lo >= 8 ? 0u : (m & (0xFFu << lo));
-        if (__ballot_sync(0xFFFFFFFFu, m != 0) == 0) continue;
+        if (lo > 0) {
+            const unsigned keep = lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+            sure &= keep;
+            amb &= keep;
+        }
+        if (__ballot_sync(0xFFFFFFFFu, (sure | amb) != 0) == 0) continue;
         bool found = false;
         int fa = -1;
         for (;;) {
+            const unsigned m = sure | amb;
             if (m != 0 && !found) {
-                const int a = idx + __ffs(m) - 1;
-                const unsigned long long key = ld_relaxed_u64(prop + a);
-                if ((unsigned)(key >> 32) < r) {
-                    m &= m - 1;  // taken in an earlier round
-                } else {
+                const int j = __ffs(m) - 1;
+                if (sure & (1u << j)) {
                     found = true;
-                    fa = a;
+                    fa = idx + j;
+                } else {
+                    // order this word read after the key read that showed +1
+                    __threadfence();
+                    const unsigned long long w = ld_relaxed_u64(prop + idx + j);
+                    if (tag_of(w) == R) {
+                        found = true;
+                        fa = idx + j;
+                    } else {
+                        amb &= ~(1u << j);
+                    }
                 }
             }
-            const unsigned inplay = __ballot_sync(0xFFFFFFFFu, m != 0 || found);
+            const unsigned inplay = __ballot_sync(0xFFFFFFFFu, (sure | amb) != 0 || found);
             if (inplay == 0) break;
             const int L = __ffs(inplay) - 1;
             const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
@@ -221,51 +277,102 @@ __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
 }
 
 // ---------------------------------------------------------------------------
-// Shared state of one CTA of the phase kernel.
+// Per-CTA lists: the first kListSm entries in shared memory, the rest in the
+// CTA's private region of the workspace.
 // ---------------------------------------------------------------------------
 struct Smem {
-    int job_b[kQueue];
-    int job_start[kQueue];
-    int buf_prop[kQueue];
-    int buf_free[kQueue];
-    int buf_won[kQueue];
-    int n_job, n_prop, n_free, n_won;
+    int fl[2][kListSm];       // rows of this phase / next phase
+    int2 ql[2][kListSm];      // (b, a) proposals of this round / previous round
+    int job_b[kBatch];
+    int job_start[kBatch];
     int best[kWarps];
-    int base_prop, base_free, base_won;
+    int nfl[2], nql[2];
+    int njob;
+    int had_prop, nonfirst, nf_delta;
     unsigned long long bytes;
     unsigned long long rows;
+    unsigned long long pub;
+    int err;
 };
 
-__device__ __forceinline__ void flush_lists(Smem &s, const Params &p, int *prop_list,
-                                            int *prop_cnt, int *free_list, int *free_cnt,
-                                            int *won_list, int *won_cnt) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s.base_prop = s.n_prop ? atomicAdd(prop_cnt, s.n_prop) : 0;
-        s.base_free = s.n_free ? atomicAdd(free_cnt, s.n_free) : 0;
-        s.base_won = s.n_won ? atomicAdd(won_cnt, s.n_won) : 0;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < s.n_prop; i += blockDim.x) prop_list[s.base_prop + i] = s.buf_prop[i];
-    for (int i = threadIdx.x; i < s.n_free; i += blockDim.x) free_list[s.base_free + i] = s.buf_free[i];
-    for (int i = threadIdx.x; i < s.n_won; i += blockDim.x) won_list[s.base_won + i] = s.buf_won[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s.n_prop = 0;
-        s.n_free = 0;
-        s.n_won = 0;
-        s.n_job = 0;
-    }
-    __syncthreads();
+struct Lists {
+    int *fl[2];   // global overflow of fl
+    int2 *ql[2];  // global overflow of ql
+};
+
+__device__ __forceinline__ void fl_push(Smem &s, const Lists &g, int which, int v) {
+    const int i = atomicAdd(&s.nfl[which], 1);
+    if (i < kListSm) s.fl[which][i] = v;
+    else g.fl[which][i - kListSm] = v;
+}
+__device__ __forceinline__ int fl_get(const Smem &s, const Lists &g, int which, int i) {
+    return i < kListSm ? s.fl[which][i] : g.fl[which][i - kListSm];
+}
+__device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a) {
+    const int i = atomicAdd(&s.nql[which], 1);
+    if (i < kListSm) s.ql[which][i] = make_int2(b, a);
+    else g.ql[which][i - kListSm] = make_int2(b, a);
+}
+__device__ __forceinline__ int2 ql_get(const Smem &s, const Lists &g, int which, int i) {
+    return i < kListSm ? s.ql[which][i] : g.ql[which][i - kListSm];
 }
 
-// Scan the queued jobs (row b from column `start`), rows_per_group rows at a
-// time, warps_per_row warps per row; then propose or relabel.
-__device__ __forceinline__ void run_jobs(Smem &s, const Params &p, const uint16_t *ks,
-                                         unsigned long long *prop, unsigned r, int q_phase,
-                                         int warps_per_row, int rows_per_group) {
+// Grid barrier carrying a payload: each CTA adds
+//   1 (arrival) | had_prop << 10 | nonfirst << 20 | nf_delta << 40
+// (had_prop, nonfirst in {0,1}; nf_delta < 2^24) to one 64-bit accumulator.
+// The last arrival resets it and publishes (gen << 32) | (P>0) << 31 |
+// (L>0) << 30 | sum(nf_delta) with a release store; the others spin (bounded)
+// on the published word.  Returns false when the kernel must stop.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsigned G,
+                                          long long limit, unsigned long long mine) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = gen + 1;
+        __threadfence();
+        const unsigned long long old = atomicAdd(&ctl->bar_acc, mine);
+        unsigned long long pub = 0;
+        if ((old & 1023ull) == (unsigned long long)(G - 1)) {
+            const unsigned long long tot = old + mine;
+            const unsigned long long P = (tot >> 10) & 1023ull;
+            const unsigned long long L = (tot >> 20) & 1023ull;
+            const unsigned long long nf = (tot >> 40) & 0xFFFFFFull;
+            ctl->bar_acc = 0;
+            pub = ((unsigned long long)g << 32) | ((P ? 1ull : 0ull) << 31) |
+                  ((L ? 1ull : 0ull) << 30) | nf;
+            __threadfence();
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&ctl->bar_pub), "l"(pub)
+                         : "memory");
+        } else {
+            const long long t0 = clock64();
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+                             : "=l"(pub)
+                             : "l"(&ctl->bar_pub)
+                             : "memory");
+                if ((unsigned)(pub >> 32) == g) break;
+                if (ld_relaxed_s32(&ctl->head.abort)) break;
+                if (clock64() - t0 > limit) {
+                    record_error(&ctl->head, PR_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s.pub = pub;
+        s.err = ld_relaxed_s32(&ctl->head.abort);
+    }
+    __syncthreads();
+    gen += 1;
+    return s.err == 0 && (unsigned)(s.pub >> 32) == gen;
+}
+
+// Scan queued jobs rows_per_group rows at a time with warps_per_row warps per
+// row, then propose (atomicMax) or relabel.
+__device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p, unsigned R,
+                                         unsigned Rps, int cur, int qcur, int warps_per_row,
+                                         int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nq = s.n_job;
+    const int nq = s.njob;
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
         const int ng = min(rows_per_group, nq - g0);
         if (threadIdx.x < ng) s.best[threadIdx.x] = 0x7FFFFFFF;
@@ -276,15 +383,14 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Params &p, const uint16_
             const int b = s.job_b[g0 + slot];
             const int start = s.job_start[g0 + slot];
             const int s8 = start & ~7;
-            const uint32_t tgt = (uint32_t)(p.y_b[b] - 1);
-            const uint32_t tgt2 = tgt | (tgt << 16);
+            const uint32_t tgt = (uint32_t)(ld_relaxed_s32(p.y_b + b) - 1);
             const uint16_t *row = p.cb + (size_t)b * p.ldq;
             volatile int *vbest = &s.best[slot];
             for (int c0 = s8 + sub * kChunk; c0 < p.ldq; c0 += warps_per_row * kChunk) {
                 // warp-uniform early exit: lane 0's view of the row's best so far
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
                 my_bytes += 2ull * (unsigned long long)min(kChunk, p.ldq - c0);
-                const int a = warp_scan_chunk(row, ks, c0, start, p.ldq, tgt2, prop, r, lane);
+                const int a = warp_scan_chunk(row, p.ka, c0, start, p.ldq, tgt, p.prop, R, lane);
                 if (a >= 0) {
                     if (lane == 0) atomicMin(&s.best[slot], a);
                     break;
@@ -297,147 +403,148 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Params &p, const uint16_
             const int b = s.job_b[g0 + threadIdx.x];
             const int a = s.best[threadIdx.x];
             if (a != 0x7FFFFFFF) {
-                atomicMin(prop + a, ((unsigned long long)r << 32) | (unsigned)b);
-                p.ptr[b] = a;
-                s.buf_prop[atomicAdd(&s.n_prop, 1)] = b;
+                const unsigned long long old = atomicMax(p.prop + a, word_of(R, b));
+                const unsigned t = tag_of(old);
+                if (t < Rps) {
+                    // first proposal to a in this phase: a is won this round
+                    // (step III a: y(a) -= eps) and its old partner is evicted
+                    // (step II) into the next phase's B'.
+                    __threadfence();
+                    // +1 on the 16-bit key at L2 (no carry leaves the half: k <= 32768)
+                    atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
+                    const int partner = row_of(old);
+                    if (partner >= 0) {
+                        fl_push(s, g, cur ^ 1, partner);
+                        atomicAdd(&s.nf_delta, 1);
+                    }
+                } else if (t == R) {
+                    s.nonfirst = 1;
+                } else {
+                    record_error(&p.ctl->head, PR_ERR_INTERNAL);
+                }
+                ql_push(s, g, qcur, b, a);
+                s.had_prop = 1;
             } else {
-                p.y_b[b] += 1;  // step (III b): free w.r.t. M' -> relabel
-                s.buf_free[atomicAdd(&s.n_free, 1)] = b;
+                atomicAdd(p.y_b + b, 1);  // step (III b): free w.r.t. M' -> relabel
+                fl_push(s, g, cur ^ 1, b);
+                atomicAdd(&s.nf_delta, 1);
             }
         }
-        // the next group's reset of s.best is ordered by the barrier at its top
         __syncthreads();
     }
-    if (threadIdx.x == 0) s.rows += (unsigned long long)nq;
+    if (threadIdx.x == 0) {
+        s.rows += (unsigned long long)nq;
+        s.njob = 0;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // k_phases: every phase of Sec. 2.2 in one cooperative launch.
 //
-// Phase p (parity q = p & 1) works on B' = freel[p % 3].  Step 1 scans every
-// row of B' from column 0.  Step s >= 2 first settles the proposals of step
-// s-1: the winner of column a (lowest proposer, atomicMin of (round<<32 | b))
-// pushes (a,b) into M, evicts a's old partner into next B' and lowers y(a);
-// a loser rescans its row after a.  A row with no admissible untaken column
-// relabels (y(b) += 1) and joins next B'.  The phase ends after the first
-// step in which nobody proposed; one grid barrier separates steps.
+// Each CTA owns a set of free rows.  Phase 0 deals rows b = cta + k*G.  A row
+// that relabels stays with its CTA for the next phase; a row evicted by a
+// first proposal joins that proposer's CTA.  Round R of a phase scans the
+// CTA's jobs (all its rows in the first round; afterwards the rows whose
+// proposal lost, resuming after the lost column), then one payload barrier.
+// If no column received two proposals in round R every proposal won and the
+// phase is over; otherwise each CTA rereads its proposals' words to find the
+// losers and runs round R + 1.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
-    __shared__ Smem s;
-    uint16_t *ks = reinterpret_cast<uint16_t *>(dyn);  // k(a) as of the phase start
+    Smem &s = *reinterpret_cast<Smem *>(dyn);
     Ctl *ctl = p.ctl;
-    WsHead *head = &ctl->head;
     const unsigned G = gridDim.x;
-    unsigned gen = 0;
+    const int cta = blockIdx.x;
+    Lists g;
+    int *base = p.lists + (size_t)cta * p.list_stride;
+    g.fl[0] = base;
+    g.fl[1] = base + p.nB;
+    g.ql[0] = reinterpret_cast<int2 *>(base + 2 * (size_t)p.nB);
+    g.ql[1] = reinterpret_cast<int2 *>(base + 4 * (size_t)p.nB);
 
-    for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
-        reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
     if (threadIdx.x == 0) {
-        s.n_job = s.n_prop = s.n_free = s.n_won = 0;
-        s.bytes = 0;
-        s.rows = 0;
+        s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
+        s.njob = 0;
+        s.bytes = s.rows = 0;
+        s.err = 0;
     }
     __syncthreads();
 
-    long long phase = 0;
-    unsigned long long step = 0;
-    long long rounds = 0;
+    unsigned gen = 0;
+    unsigned R = 0;  // global round counter (round tags)
+    long long phase = 0, rounds = 0;
+    int cur = 0, qcur = 0;
+    const int first_items = cta < p.nB ? (p.nB - 1 - cta) / (int)G + 1 : 0;
     for (;;) {
-        const int cur = (int)(phase % 3);
-        const int nf = ld_relaxed_s32(&ctl->nfree[cur]);
-        if (nf <= p.T) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->free_at_stop = nf;
-            break;
-        }
-        if (phase >= p.phase_cap) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                ctl->free_at_stop = nf;
-                record_error(head, PR_ERR_NO_CONVERGENCE);
-            }
-            break;
-        }
-        const int q = (int)(phase & 1);
-        unsigned long long *prop = p.prop + (size_t)q * p.nA;
-        unsigned long long *prop_old = p.prop + (size_t)(q ^ 1) * p.nA;
-        int *won_list = p.wonl + (size_t)q * p.nB;
-        const int *won_old = p.wonl + (size_t)(q ^ 1) * p.nB;
-        const int nxt = (int)((phase + 1) % 3);
-        int *free_next = p.freel + (size_t)nxt * p.nB;
-
-        // Phase start: columns won in the previous phase have k(a) one higher
-        // (step III a); their proposal words are reset for phase p + 1.
-        {
-            const int nw = phase > 0 ? ld_relaxed_s32(&ctl->nwon[q ^ 1]) : 0;
-            for (int i = threadIdx.x; i < nw; i += blockDim.x) ks[won_old[i]] += 1;
-            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += G * blockDim.x)
-                prop_old[won_old[i]] = kEmpty;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                ctl->nwon[q] = 0;
-                ctl->nfree[(phase + 2) % 3] = 0;
+        // ---- one phase ----
+        const unsigned Rps = R + 1;
+        long long nf_next = 0;
+        bool first_round = true;
+        for (;;) {
+            ++R;
+            if (threadIdx.x == 0) {
+                s.had_prop = 0;
+                s.nonfirst = 0;
+                s.nf_delta = 0;
+                s.nql[qcur] = 0;
             }
             __syncthreads();
-        }
-
-        const int *work = p.freel + (size_t)cur * p.nB;
-        int nwork = nf;
-        unsigned r = 0;
-        for (;;) {
-            ++r;
-            ++step;
-            const int si = (int)(step % 3);
-            int *prop_list = p.propl + (size_t)si * p.nB;
-            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nprop[(step + 1) % 3] = 0;
-
-            // this CTA's items: work[blockIdx.x + k * G], k = 0, 1, ... (cyclic)
-            const int my_items = nwork > (int)blockIdx.x ? (nwork - 1 - (int)blockIdx.x) / (int)G + 1 : 0;
-            for (int k0 = 0; k0 < my_items; k0 += kQueue) {
-                const int cnt = min(kQueue, my_items - k0);
+            // items of this round: the phase's rows, or last round's proposals
+            const int nitems = first_round ? (phase == 0 ? first_items : s.nfl[cur]) : s.nql[qcur ^ 1];
+            for (int i0 = 0; i0 < nitems; i0 += kBatch) {
+                const int cnt = min(kBatch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                    const int b = work[blockIdx.x + (size_t)(k0 + i) * G];
-                    int start = 0;
-                    if (r > 1) {
-                        const int a = p.ptr[b];
-                        const unsigned long long key = ld_relaxed_u64(prop + a);
-                        if (key == (((unsigned long long)(r - 1) << 32) | (unsigned)b)) {
-                            // Step (II): push (a,b), evict a's old partner.
-                            const int old = p.match_a[a];
-                            if (old >= 0) {
-                                p.match_b[old] = -1;
-                                s.buf_free[atomicAdd(&s.n_free, 1)] = old;
-                            }
-                            p.match_a[a] = b;
-                            p.match_b[b] = a;
-                            p.ka[a] += 1;  // step (III a): y(a) -= eps
-                            s.buf_won[atomicAdd(&s.n_won, 1)] = a;
-                            continue;
-                        }
-                        start = a + 1;  // lost: resume after a
+                    int b, start = 0;
+                    if (first_round) {
+                        b = phase == 0 ? cta + (i0 + i) * (int)G : fl_get(s, g, cur, i0 + i);
+                    } else {
+                        const int2 q = ql_get(s, g, qcur ^ 1, i0 + i);
+                        b = q.x;
+                        const unsigned long long w = ld_relaxed_u64(p.prop + q.y);
+                        if (row_of(w) == b) continue;  // won: matched, leaves B'
+                        start = q.y + 1;               // lost: resume after a
                     }
-                    const int j = atomicAdd(&s.n_job, 1);
+                    const int j = atomicAdd(&s.njob, 1);
                     s.job_b[j] = b;
                     s.job_start[j] = start;
                 }
                 __syncthreads();
-                run_jobs(s, p, ks, prop, r, q, warps_per_row, rows_per_group);
-                flush_lists(s, p, prop_list, &ctl->nprop[si], free_next, &ctl->nfree[nxt], won_list,
-                            &ctl->nwon[q]);
+                run_jobs(s, g, p, R, Rps, cur, qcur, warps_per_row, rows_per_group);
             }
-            if (!grid_barrier(head, gen, G, p.spin_limit)) goto done;
-            const int np = ld_relaxed_s32(&ctl->nprop[si]);
-            if (np == 0) break;
-            ++rounds;
-            work = prop_list;
-            nwork = np;
+            const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
+                                            ((unsigned long long)s.nonfirst << 20) |
+                                            ((unsigned long long)s.nf_delta << 40);
+            if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine)) goto done;
+            const unsigned long long pub = s.pub;
+            if ((pub >> 31) & 1ull) ++rounds;
+            nf_next += (long long)(pub & 0x3FFFFFFFull);
+            first_round = false;
+            qcur ^= 1;
+            if (!((pub >> 30) & 1ull)) break;  // no contested column: phase over
         }
         ++phase;
+        if (threadIdx.x == 0) s.nfl[cur] = 0;
+        cur ^= 1;
+        if (nf_next <= p.T) {
+            if (cta == 0 && threadIdx.x == 0) ctl->free_at_stop = (int)nf_next;
+            break;
+        }
+        if (phase >= p.phase_cap) {
+            if (cta == 0 && threadIdx.x == 0) {
+                ctl->free_at_stop = (int)nf_next;
+                record_error(&ctl->head, PR_ERR_NO_CONVERGENCE);
+            }
+            break;
+        }
     }
 done:
     if (threadIdx.x == 0) {
         if (s.bytes) atomicAdd(&ctl->bytes, s.bytes);
         if (s.rows) atomicAdd(&ctl->rows, s.rows);
-        if (blockIdx.x == 0) {
+        if (cta == 0) {
             ctl->phases = phase;
             ctl->rounds = rounds;
         }
@@ -445,8 +552,23 @@ done:
 }
 
 // ---------------------------------------------------------------------------
-// k_finish (one CTA): completion (k-th free row with k-th free column),
-// y(A) = -k, and the FP64 matching cost with a fixed-order tree reduction.
+// k_decode: the matching is the per-column words' rows; y(A) = -k.
+// ---------------------------------------------------------------------------
+__global__ void k_decode(Params p, int *match_b, int *match_a, int *y_col) {
+    if (ld_relaxed_s32(&p.ctl->head.err) != 0) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < p.nA; a += stride) {
+        const unsigned long long w = p.prop[a];
+        const int b = tag_of(w) > 0 ? row_of(w) : -1;
+        match_a[a] = b;
+        if (b >= 0) match_b[b] = a;
+        y_col[a] = -(int)p.ka[a];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_finish (one CTA): completion (k-th free row with k-th free column) and the
+// FP64 matching cost with a fixed-order tree reduction.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 1024;
 
@@ -475,17 +597,16 @@ __device__ __forceinline__ int block_exclusive_scan(int flag, int *warp_tot, int
 
 template <class T>
 __global__ void __launch_bounds__(kFinThreads)
-k_finish(Params p, const T *__restrict__ C, long long ldc, int *free_b, int *free_a,
-         int *y_col, double *cost) {
+k_finish(Params p, const T *__restrict__ C, long long ldc, int *match_b, int *match_a,
+         int *free_b, int *free_a, double *cost) {
     __shared__ int warp_tot[32];
     __shared__ int total;
     __shared__ double part[kFinThreads];
     if (ld_relaxed_s32(&p.ctl->head.err) != 0) return;
-    // ascending free rows
     int nfb = 0;
     for (int base = 0; base < p.nB; base += kFinThreads) {
         const int b = base + threadIdx.x;
-        const int f = (b < p.nB && p.match_b[b] < 0) ? 1 : 0;
+        const int f = (b < p.nB && match_b[b] < 0) ? 1 : 0;
         const int pos = block_exclusive_scan(f, warp_tot, &total);
         if (f) free_b[nfb + pos] = b;
         nfb += total;
@@ -494,21 +615,20 @@ k_finish(Params p, const T *__restrict__ C, long long ldc, int *free_b, int *fre
     int nfa = 0;
     for (int base = 0; base < p.nA && nfa < nfb; base += kFinThreads) {
         const int a = base + threadIdx.x;
-        const int f = (a < p.nA && p.match_a[a] < 0) ? 1 : 0;
+        const int f = (a < p.nA && match_a[a] < 0) ? 1 : 0;
         const int pos = block_exclusive_scan(f, warp_tot, &total);
         if (f && nfa + pos < nfb) free_a[nfa + pos] = a;
         nfa += total;
         __syncthreads();
     }
     for (int k = threadIdx.x; k < nfb; k += kFinThreads) {
-        p.match_b[free_b[k]] = free_a[k];
-        p.match_a[free_a[k]] = free_b[k];
+        match_b[free_b[k]] = free_a[k];
+        match_a[free_a[k]] = free_b[k];
     }
-    for (int a = threadIdx.x; a < p.nA; a += kFinThreads) y_col[a] = -(int)p.ka[a];
     __syncthreads();
     double acc = 0.0;
     for (int b = threadIdx.x; b < p.nB; b += kFinThreads)
-        acc = __dadd_rn(acc, (double)C[(long long)b * ldc + p.match_b[b]]);
+        acc = __dadd_rn(acc, (double)C[(long long)b * ldc + match_b[b]]);
     part[threadIdx.x] = acc;
     __syncthreads();
     for (int w = kFinThreads / 2; w > 0; w >>= 1) {
@@ -521,44 +641,46 @@ k_finish(Params p, const T *__restrict__ C, long long ldc, int *free_b, int *fre
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-struct KernelCfg {
+struct PhaseCfg {
     int grid = 0;
-    int dev = -1;
     size_t smem = 0;
 };
 
-pr_status launch_phases(const Params &prm, int ldq, cudaStream_t st) {
+pr_status phase_cfg(PhaseCfg &cfg) {
+    static int cached_dev = -1;
+    static PhaseCfg cached;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (dev == cached_dev) {
+        cfg = cached;
+        return PR_OK;
+    }
     const DeviceInfo &di = device_info();
-    const size_t smem = (size_t)ldq * sizeof(uint16_t);
-    if (smem + sizeof(Smem) > (size_t)di.max_smem_optin)
-        return fail(PR_ERR_INVALID, "n_cols too large for the shared-memory key copy");
+    const size_t smem = sizeof(Smem);
+    if (smem > (size_t)di.max_smem_optin) return fail(PR_ERR_INVALID, "phase kernel shared memory too large");
     PR_CUDA(cudaFuncSetAttribute(k_phases, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases, kThreads, smem));
     if (per_sm < 1) return fail(PR_ERR_INVALID, "phase kernel does not fit on an SM");
-    const int grid = di.sms * per_sm;
-    const int chunks = (ldq + kChunk - 1) / kChunk;
-    int warps_per_row = chunks < kWarps ? chunks : kWarps;
-    int rows_per_group = kWarps / warps_per_row;
-    Params pc = prm;
-    void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
-    PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(grid), dim3(kThreads), args,
-                                        smem, st));
+    int grid = di.sms * per_sm;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    cfg.grid = grid;
+    cfg.smem = smem;
+    cached = cfg;
+    cached_dev = dev;
     return PR_OK;
 }
 
 }  // namespace
-
-// Exposed to the other translation units (batched solver reuses the layout).
-size_t assign_workspace_bytes(int nB, int nA) { return make_layout(nB, nA).total; }
-
 }  // namespace prot
 
 using namespace prot;
 
 extern "C" size_t pr_assign_workspace(int32_t n_rows, int32_t n_cols) {
-    if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24)) return 0;
-    return make_layout(n_rows, n_cols).total;
+    if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24) - 1) return 0;
+    PhaseCfg cfg;
+    if (phase_cfg(cfg) != PR_OK) cfg.grid = kMaxGrid;  // no device: the largest grid
+    return make_layout(n_rows, n_cols, cfg.grid).total;
 }
 
 extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
@@ -568,12 +690,15 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     if (!C || !row_to_col || !col_to_row || !y_row || !y_col || !cost)
         return fail(PR_ERR_INVALID, "pr_assign: NULL pointer argument");
     if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign: bad dtype");
-    if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24))
-        return fail(PR_ERR_INVALID, "pr_assign: need 1 <= n_rows <= n_cols <= 2^24");
+    if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24) - 1)
+        return fail(PR_ERR_INVALID, "pr_assign: need 1 <= n_rows <= n_cols < 2^24");
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign: ldc < n_cols");
     if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
         return fail(PR_ERR_INVALID, "pr_assign: need 0 < eps < 1 and floor(1/eps) <= 32766");
-    const Layout L = make_layout(n_rows, n_cols);
+    PhaseCfg cfg;
+    pr_status rc = phase_cfg(cfg);
+    if (rc != PR_OK) return rc;
+    const Layout L = make_layout(n_rows, n_cols, cfg.grid);
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
         return fail(PR_ERR_WORKSPACE, "pr_assign: workspace NULL, not 256-byte aligned or < %zu bytes",
                     L.total);
@@ -585,13 +710,9 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.cb = (const uint16_t *)(w + L.cb);
     p.ka = (uint16_t *)(w + L.ka);
     p.y_b = y_row;
-    p.match_b = row_to_col;
-    p.match_a = col_to_row;
-    p.ptr = (int *)(w + L.ptr);
     p.prop = (unsigned long long *)(w + L.prop);
-    p.freel = (int *)(w + L.freel);
-    p.propl = (int *)(w + L.propl);
-    p.wonl = (int *)(w + L.wonl);
+    p.lists = (int *)(w + L.lists);
+    p.list_stride = L.list_stride;
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
@@ -601,30 +722,45 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.spin_limit = spin_limit_cycles();
 
     const DeviceInfo &di = device_info();
-    k_init<<<di.sms * 2, 256, 0, st>>>(p);
+    k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
     PR_CUDA(cudaGetLastError());
     const long long groups = (long long)n_rows * (L.ldq >> 3);
-    const int qgrid = (int)(groups / 256 + 1 < (long long)di.sms * 8 ? groups / 256 + 1 : di.sms * 8);
+    const long long want = groups / 256 + 1;
+    const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
+    const float inv_eps = (float)(1.0 / eps);
     if (dt == PR_F64)
         k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                  (uint16_t *)p.cb, &p.ctl->head);
+                                                  inv_eps, (uint16_t *)p.cb, &p.ctl->head);
     else
         k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                 (uint16_t *)p.cb, &p.ctl->head);
+                                                 inv_eps, (uint16_t *)p.cb, &p.ctl->head);
     PR_CUDA(cudaGetLastError());
+
+    const int chunks = (L.ldq + kChunk - 1) / kChunk;
+    int warps_per_row = chunks < kWarps ? chunks : kWarps;
+    int rows_per_group = kWarps / warps_per_row;
     cudaEvent_t ev0, ev1;
     kernel_events(&ev0, &ev1);
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev0, st));
-    pr_status rc = launch_phases(p, L.ldq, st);
-    if (rc != PR_OK) return rc;
+    {
+        Params pc = p;
+        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
+        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(cfg.grid), dim3(kThreads),
+                                            args, cfg.smem, st));
+    }
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
-    // completion lists reuse the proposer-list region (free after the loop)
-    int *free_b = p.propl;
-    int *free_a = p.propl + n_rows;  // 3*nB ints available; free_a needs <= nB entries
+
+    k_decode<<<di.sms * 2, 256, 0, st>>>(p, row_to_col, col_to_row, y_col);
+    PR_CUDA(cudaGetLastError());
+    // completion scratch: the first CTA's list region (free after the loop)
+    int *free_b = p.lists;
+    int *free_a = p.lists + n_rows;
     if (dt == PR_F64)
-        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, free_b, free_a, y_col, cost);
+        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
+                                                    free_b, free_a, cost);
     else
-        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, free_b, free_a, y_col, cost);
+        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
+                                                   free_b, free_a, cost);
     PR_CUDA(cudaGetLastError());
 
     if (stats) {
