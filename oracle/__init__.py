@@ -109,7 +109,7 @@ def _declare(L):
     if hasattr(L, "or_ot_cluster"):
         from . import ot as _ot  # noqa: F401  (declares its own symbols)
         _ot._declare(L)
-    if hasattr(L, "or_cost_from_points"):
+    if hasattr(L, "or_assign_points"):
         from . import points as _pts
         _pts._declare(L)
 

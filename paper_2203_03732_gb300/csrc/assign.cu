@@ -22,6 +22,12 @@
 // a column last won in an earlier phase names its current partner, so the
 // first proposer of a phase learns from atomicMax's return value both that
 // it is first and which row step (II) evicts.  Nothing is ever reset.
+//
+// The duals y(A) must stay fixed within a phase.  Each CTA keeps its own
+// shared-memory copy of k(A); the first proposer of a column sets the
+// column's bit in the phase's "won" bitmap (step III a), and at the start of
+// the next phase every CTA adds the bitmap to its copy.  Bitmaps rotate over
+// three buffers so one is cleared while the next is read.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -56,8 +62,8 @@ struct Ctl {
 };
 
 struct Layout {
-    size_t ctl, cb, ka, prop, lists, total;
-    int ldq;
+    size_t ctl, cb, ka, prop, won, lists, total;
+    int ldq, won_words;
     size_t list_stride;  // ints per CTA in the list region
 };
 
@@ -72,6 +78,8 @@ Layout make_layout(int nB, int nA, int grid) {
     L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
     L.ka = c.take<uint16_t>(L.ldq);
     L.prop = c.take<unsigned long long>((size_t)nA);
+    L.won_words = (nA + 31) / 32;
+    L.won = c.take<unsigned>(3 * (size_t)L.won_words);
     L.list_stride = 6 * (size_t)nB;
     L.lists = c.take<int>((size_t)grid * L.list_stride);
     L.total = c.total();
@@ -84,6 +92,8 @@ struct Params {
     uint16_t *ka;
     int *y_b;
     unsigned long long *prop;
+    unsigned *won;  // [3][won_words]
+    int won_words;
     int *lists;
     size_t list_stride;
     int nB, nA, ldq, T;
@@ -111,6 +121,7 @@ __global__ void k_init(Params p, int *match_b) {
         p.ka[a] = a < p.nA ? 0 : kPadKey;
         if (a < p.nA) p.prop[a] = word_of(0, -1);  // round 0, no partner
     }
+    for (int i = t0; i < 3 * p.won_words; i += stride) p.won[i] = 0;
     if (t0 == 0) {
         Ctl *c = p.ctl;
         memset(c, 0, sizeof(Ctl));
@@ -176,22 +187,11 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
 }
 
 // ---------------------------------------------------------------------------
-// Row scan.  For the phase-start keys k0, the edge (a,b) is admissible iff
-// cbar + k0(a) == tgt.  The keys read here may already carry the +1 of a
-// column first proposed to in the current round (the +1 of an earlier round
-// of the phase is always visible: a grid barrier separates them), and
-// feasibility (I2) gives cbar + k0 >= tgt for a free row.  Hence:
-//   seen == tgt     -> admissible and not taken: a candidate;
-//   seen == tgt + 1 -> admissible iff a was proposed to in this phase, and a
-//                      candidate iff that happened in this very round R.
+// Row scan against the phase's fixed keys ks (shared memory): the edge (a,b)
+// is admissible iff cbar + k(a) == tgt = y(b) - 1.  In the first round of a
+// phase nothing is taken; in later rounds a candidate column is skipped when
+// its word carries a tag of an earlier round of this phase.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 ld_cg_v4(const void *p) {
-    uint4 v;
-    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
 __device__ __forceinline__ uint4 ld_nc_na_v4(const void *p) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -215,58 +215,51 @@ __device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
 }
 
 // Lowest candidate column in [c0, c0 + kChunk) that is >= start, or -1.
-__device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ka,
+__device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ks,
                                                int c0, int start, int ldq, uint32_t tgt,
                                                const unsigned long long *prop, unsigned R,
-                                               int lane) {
+                                               unsigned Rps, int lane) {
     uint4 sv[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int idx = c0 + u * 256 + lane * 8;
         if (idx < ldq) {
             const uint4 c = ld_nc_na_v4(row + idx);
-            const uint4 k = ld_cg_v4(ka + idx);
+            const uint4 k = *reinterpret_cast<const uint4 *>(ks + idx);
             sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
         } else {
             sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         }
     }
     const uint32_t t2 = tgt | (tgt << 16);
-    const uint32_t t2p = (tgt + 1) | ((tgt + 1) << 16);
+    const bool check_taken = R > Rps;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int idx = c0 + u * 256 + lane * 8;
-        unsigned sure = eq_mask(sv[u], t2);
-        unsigned amb = eq_mask(sv[u], t2p);
+        unsigned m = eq_mask(sv[u], t2);
         const int lo = start - idx;
-        if (lo > 0) {
-            const unsigned keep = lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
-            sure &= keep;
-            amb &= keep;
+        if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
+        if (any == 0) continue;
+        if (!check_taken) {
+            const int L = __ffs(any) - 1;
+            const int a = idx + __ffs(m) - 1;  // meaningful in lane L
+            return __shfl_sync(0xFFFFFFFFu, a, L);
         }
-        if (__ballot_sync(0xFFFFFFFFu, (sure | amb) != 0) == 0) continue;
         bool found = false;
         int fa = -1;
         for (;;) {
-            const unsigned m = sure | amb;
             if (m != 0 && !found) {
-                const int j = __ffs(m) - 1;
-                if (sure & (1u << j)) {
-                    found = true;
-                    fa = idx + j;
+                const int a = idx + __ffs(m) - 1;
+                const unsigned t = tag_of(ld_relaxed_u64(prop + a));
+                if (t >= Rps && t < R) {
+                    m &= m - 1;  // taken in an earlier round of this phase
                 } else {
-                    // order this word read after the key read that showed +1
-                    __threadfence();
-                    const unsigned long long w = ld_relaxed_u64(prop + idx + j);
-                    if (tag_of(w) == R) {
-                        found = true;
-                        fa = idx + j;
-                    } else {
-                        amb &= ~(1u << j);
-                    }
+                    found = true;
+                    fa = a;
                 }
             }
-            const unsigned inplay = __ballot_sync(0xFFFFFFFFu, (sure | amb) != 0 || found);
+            const unsigned inplay = __ballot_sync(0xFFFFFFFFu, m != 0 || found);
             if (inplay == 0) break;
             const int L = __ffs(inplay) - 1;
             const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
@@ -368,7 +361,8 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
 
 // Scan queued jobs rows_per_group rows at a time with warps_per_row warps per
 // row, then propose (atomicMax) or relabel.
-__device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p, unsigned R,
+__device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
+                                         const uint16_t *ks, unsigned *won_now, unsigned R,
                                          unsigned Rps, int cur, int qcur, int warps_per_row,
                                          int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -390,7 +384,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 // warp-uniform early exit: lane 0's view of the row's best so far
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
                 my_bytes += 2ull * (unsigned long long)min(kChunk, p.ldq - c0);
-                const int a = warp_scan_chunk(row, p.ka, c0, start, p.ldq, tgt, p.prop, R, lane);
+                const int a = warp_scan_chunk(row, ks, c0, start, p.ldq, tgt, p.prop, R, Rps, lane);
                 if (a >= 0) {
                     if (lane == 0) atomicMin(&s.best[slot], a);
                     break;
@@ -407,10 +401,11 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 const unsigned t = tag_of(old);
                 if (t < Rps) {
                     // first proposal to a in this phase: a is won this round
-                    // (step III a: y(a) -= eps) and its old partner is evicted
-                    // (step II) into the next phase's B'.
-                    __threadfence();
-                    // +1 on the 16-bit key at L2 (no carry leaves the half: k <= 32768)
+                    // (step III a: y(a) -= eps, applied to the key copies at
+                    // the next phase) and its old partner is evicted (step II)
+                    // into the next phase's B'.
+                    atomicOr(won_now + (a >> 5), 1u << (a & 31));
+                    // +1 on the 16-bit output key at L2 (no carry leaves the half: k <= 32768)
                     atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
                     const int partner = row_of(old);
                     if (partner >= 0) {
@@ -455,6 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
     Smem &s = *reinterpret_cast<Smem *>(dyn);
+    uint16_t *ks = reinterpret_cast<uint16_t *>(dyn + ((sizeof(Smem) + 15) & ~size_t(15)));
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
@@ -465,6 +461,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     g.ql[0] = reinterpret_cast<int2 *>(base + 2 * (size_t)p.nB);
     g.ql[1] = reinterpret_cast<int2 *>(base + 4 * (size_t)p.nB);
 
+    for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
+        reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
     if (threadIdx.x == 0) {
         s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
         s.njob = 0;
@@ -481,6 +479,23 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     for (;;) {
         // ---- one phase ----
         const unsigned Rps = R + 1;
+        unsigned *won_now = p.won + (size_t)(phase % 3) * p.won_words;
+        if (phase > 0) {
+            // step (III a) of the previous phase reaches this CTA's keys
+            const unsigned *won_prev = p.won + (size_t)((phase + 2) % 3) * p.won_words;
+            for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) {
+                unsigned m = ld_relaxed_u32(won_prev + i);
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    ks[i * 32 + bit] += 1;
+                    m &= m - 1;
+                }
+            }
+            // the bitmap of two phases ago has been read by every CTA
+            unsigned *won_old = p.won + (size_t)((phase + 1) % 3) * p.won_words;
+            for (int i = cta * blockDim.x + threadIdx.x; i < p.won_words; i += G * blockDim.x)
+                won_old[i] = 0;
+        }
         long long nf_next = 0;
         bool first_round = true;
         for (;;) {
@@ -512,7 +527,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     s.job_start[j] = start;
                 }
                 __syncthreads();
-                run_jobs(s, g, p, R, Rps, cur, qcur, warps_per_row, rows_per_group);
+                run_jobs(s, g, p, ks, won_now, R, Rps, cur, qcur, warps_per_row, rows_per_group);
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
                                             ((unsigned long long)s.nonfirst << 20) |
@@ -646,6 +661,8 @@ struct PhaseCfg {
     size_t smem = 0;
 };
 
+size_t smem_bytes(int ldq) { return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)ldq * sizeof(uint16_t); }
+
 pr_status phase_cfg(PhaseCfg &cfg) {
     static int cached_dev = -1;
     static PhaseCfg cached;
@@ -656,8 +673,7 @@ pr_status phase_cfg(PhaseCfg &cfg) {
         return PR_OK;
     }
     const DeviceInfo &di = device_info();
-    const size_t smem = sizeof(Smem);
-    if (smem > (size_t)di.max_smem_optin) return fail(PR_ERR_INVALID, "phase kernel shared memory too large");
+    const size_t smem = (size_t)di.max_smem_optin;  // Smem + the key copy; see smem_bytes()
     PR_CUDA(cudaFuncSetAttribute(k_phases, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases, kThreads, smem));
@@ -665,7 +681,7 @@ pr_status phase_cfg(PhaseCfg &cfg) {
     int grid = di.sms * per_sm;
     if (grid > kMaxGrid) grid = kMaxGrid;
     cfg.grid = grid;
-    cfg.smem = smem;
+    cfg.smem = smem;  // the most a launch may ask for; each launch asks smem_bytes(ldq)
     cached = cfg;
     cached_dev = dev;
     return PR_OK;
@@ -699,6 +715,9 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     pr_status rc = phase_cfg(cfg);
     if (rc != PR_OK) return rc;
     const Layout L = make_layout(n_rows, n_cols, cfg.grid);
+    if (smem_bytes(L.ldq) > cfg.smem)
+        return fail(PR_ERR_INVALID, "pr_assign: n_cols = %d exceeds the shared-memory key copy (max %d)",
+                    n_cols, (int)((cfg.smem - smem_bytes(0)) / sizeof(uint16_t)) & ~7);
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
         return fail(PR_ERR_WORKSPACE, "pr_assign: workspace NULL, not 256-byte aligned or < %zu bytes",
                     L.total);
@@ -711,6 +730,8 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.ka = (uint16_t *)(w + L.ka);
     p.y_b = y_row;
     p.prop = (unsigned long long *)(w + L.prop);
+    p.won = (unsigned *)(w + L.won);
+    p.won_words = L.won_words;
     p.lists = (int *)(w + L.lists);
     p.list_stride = L.list_stride;
     p.nB = n_rows;
@@ -746,7 +767,7 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
         Params pc = p;
         void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
         PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(cfg.grid), dim3(kThreads),
-                                            args, cfg.smem, st));
+                                            args, smem_bytes(L.ldq), st));
     }
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
 
