@@ -24,13 +24,16 @@
 // it is first and which row step (II) evicts.  Nothing is ever reset.
 //
 // The duals y(A) must stay fixed within a phase.  Each CTA keeps its own
-// shared-memory copy of k(A); the first proposer of a column sets the
-// column's bit in the phase's "won" bitmap (step III a), and at the start of
-// the next phase every CTA adds the bitmap to its copy.  Bitmaps rotate over
-// three buffers so one is cleared while the next is read.
+// shared-memory copy of k(A) and a shared-memory bitmap of the columns taken
+// so far in the phase.  The first proposer of a column in round R sets the
+// column's bit in round R's global bitmap; at the start of round R + 1 every
+// CTA ORs that bitmap into its taken set, and at the start of a new phase it
+// adds the whole set to its keys (step III a) and empties it.  Round bitmaps
+// rotate over three buffers, so one is cleared while the next is read.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "prot_internal.cuh"
@@ -59,6 +62,9 @@ struct Ctl {
     long long rounds;
     unsigned long long bytes;
     unsigned long long rows;
+    // PR_PROFILE=1: CTA 0's %globaltimer split of the rounds (ns): round
+    // start (bitmaps, keys), items + scans + proposals, barrier; round count.
+    unsigned long long prof[4];
 };
 
 struct Layout {
@@ -92,14 +98,21 @@ struct Params {
     uint16_t *ka;
     int *y_b;
     unsigned long long *prop;
-    unsigned *won;  // [3][won_words]
+    unsigned *won;  // [3][won_words] first proposals of rounds R % 3
     int won_words;
     int *lists;
     size_t list_stride;
     int nB, nA, ldq, T;
     long long phase_cap;
     long long spin_limit;
+    int profile;
 };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
 __device__ __forceinline__ int row_of(unsigned long long w) { return (int)(0xFFFFFFFFu - (unsigned)w); }
@@ -214,11 +227,11 @@ __device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
     return m;
 }
 
-// Lowest candidate column in [c0, c0 + kChunk) that is >= start, or -1.
+// Lowest candidate column in [c0, c0 + kChunk) that is >= start and not in the
+// phase's taken set tk (shared memory; empty in a phase's first round), or -1.
 __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ks,
-                                               int c0, int start, int ldq, uint32_t tgt,
-                                               const unsigned long long *prop, unsigned R,
-                                               unsigned Rps, int lane) {
+                                               const unsigned *tk, bool check_taken, int c0,
+                                               int start, int ldq, uint32_t tgt, int lane) {
     uint4 sv[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -232,39 +245,21 @@ __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
         }
     }
     const uint32_t t2 = tgt | (tgt << 16);
-    const bool check_taken = R > Rps;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int idx = c0 + u * 256 + lane * 8;
         unsigned m = eq_mask(sv[u], t2);
         const int lo = start - idx;
         if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+        if (check_taken && m) {
+            // 8 columns idx..idx+7 lie in one 32-bit word of the bitmap
+            m &= ~(tk[idx >> 5] >> (idx & 31)) & 0xFFu;
+        }
         const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
         if (any == 0) continue;
-        if (!check_taken) {
-            const int L = __ffs(any) - 1;
-            const int a = idx + __ffs(m) - 1;  // meaningful in lane L
-            return __shfl_sync(0xFFFFFFFFu, a, L);
-        }
-        bool found = false;
-        int fa = -1;
-        for (;;) {
-            if (m != 0 && !found) {
-                const int a = idx + __ffs(m) - 1;
-                const unsigned t = tag_of(ld_relaxed_u64(prop + a));
-                if (t >= Rps && t < R) {
-                    m &= m - 1;  // taken in an earlier round of this phase
-                } else {
-                    found = true;
-                    fa = a;
-                }
-            }
-            const unsigned inplay = __ballot_sync(0xFFFFFFFFu, m != 0 || found);
-            if (inplay == 0) break;
-            const int L = __ffs(inplay) - 1;
-            const unsigned fb = __ballot_sync(0xFFFFFFFFu, found);
-            if (fb & (1u << L)) return __shfl_sync(0xFFFFFFFFu, fa, L);
-        }
+        const int L = __ffs(any) - 1;
+        const int a = idx + __ffs(m) - 1;  // meaningful in lane L
+        return __shfl_sync(0xFFFFFFFFu, a, L);
     }
     return -1;
 }
@@ -362,9 +357,9 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
 // Scan queued jobs rows_per_group rows at a time with warps_per_row warps per
 // row, then propose (atomicMax) or relabel.
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
-                                         const uint16_t *ks, unsigned *won_now, unsigned R,
-                                         unsigned Rps, int cur, int qcur, int warps_per_row,
-                                         int rows_per_group) {
+                                         const uint16_t *ks, const unsigned *tk, unsigned *won_now,
+                                         unsigned R, unsigned Rps, int cur, int qcur,
+                                         int warps_per_row, int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
@@ -384,7 +379,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 // warp-uniform early exit: lane 0's view of the row's best so far
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
                 my_bytes += 2ull * (unsigned long long)min(kChunk, p.ldq - c0);
-                const int a = warp_scan_chunk(row, ks, c0, start, p.ldq, tgt, p.prop, R, Rps, lane);
+                const int a = warp_scan_chunk(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, lane);
                 if (a >= 0) {
                     if (lane == 0) atomicMin(&s.best[slot], a);
                     break;
@@ -451,6 +446,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
     Smem &s = *reinterpret_cast<Smem *>(dyn);
     uint16_t *ks = reinterpret_cast<uint16_t *>(dyn + ((sizeof(Smem) + 15) & ~size_t(15)));
+    unsigned *tk = reinterpret_cast<unsigned *>(ks + p.ldq);  // taken set of the phase
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
@@ -463,6 +459,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
 
     for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
         reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
+    for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) tk[i] = 0;
     if (threadIdx.x == 0) {
         s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
         s.njob = 0;
@@ -479,27 +476,34 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     for (;;) {
         // ---- one phase ----
         const unsigned Rps = R + 1;
-        unsigned *won_now = p.won + (size_t)(phase % 3) * p.won_words;
-        if (phase > 0) {
-            // step (III a) of the previous phase reaches this CTA's keys
-            const unsigned *won_prev = p.won + (size_t)((phase + 2) % 3) * p.won_words;
-            for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) {
-                unsigned m = ld_relaxed_u32(won_prev + i);
-                while (m) {
-                    const int bit = __ffs(m) - 1;
-                    ks[i * 32 + bit] += 1;
-                    m &= m - 1;
-                }
-            }
-            // the bitmap of two phases ago has been read by every CTA
-            unsigned *won_old = p.won + (size_t)((phase + 1) % 3) * p.won_words;
-            for (int i = cta * blockDim.x + threadIdx.x; i < p.won_words; i += G * blockDim.x)
-                won_old[i] = 0;
-        }
         long long nf_next = 0;
         bool first_round = true;
         for (;;) {
             ++R;
+            const unsigned long long t_r0 = p.profile ? gtimer() : 0;
+            unsigned *won_now = p.won + (size_t)(R % 3) * p.won_words;
+            if (R > 1) {
+                // first proposals of round R - 1 join the taken set; a new
+                // phase first moves the finished phase's set into the keys
+                const unsigned *wprev = p.won + (size_t)((R + 2) % 3) * p.won_words;
+                for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) {
+                    unsigned m = ld_relaxed_u32(wprev + i);
+                    if (first_round) {
+                        m |= tk[i];
+                        tk[i] = 0;
+                        while (m) {
+                            ks[i * 32 + __ffs(m) - 1] += 1;
+                            m &= m - 1;
+                        }
+                    } else {
+                        tk[i] |= m;
+                    }
+                }
+                // round R - 2's bitmap has been read by every CTA: clear it for R + 1
+                unsigned *wold = p.won + (size_t)((R + 1) % 3) * p.won_words;
+                for (int i = cta * blockDim.x + threadIdx.x; i < p.won_words; i += G * blockDim.x)
+                    wold[i] = 0;
+            }
             if (threadIdx.x == 0) {
                 s.had_prop = 0;
                 s.nonfirst = 0;
@@ -507,6 +511,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 s.nql[qcur] = 0;
             }
             __syncthreads();
+            const unsigned long long t_r1 = p.profile ? gtimer() : 0;
             // items of this round: the phase's rows, or last round's proposals
             const int nitems = first_round ? (phase == 0 ? first_items : s.nfl[cur]) : s.nql[qcur ^ 1];
             for (int i0 = 0; i0 < nitems; i0 += kBatch) {
@@ -527,12 +532,20 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     s.job_start[j] = start;
                 }
                 __syncthreads();
-                run_jobs(s, g, p, ks, won_now, R, Rps, cur, qcur, warps_per_row, rows_per_group);
+                run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur, qcur, warps_per_row, rows_per_group);
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
                                             ((unsigned long long)s.nonfirst << 20) |
                                             ((unsigned long long)s.nf_delta << 40);
+            const unsigned long long t_r2 = p.profile ? gtimer() : 0;
             if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine)) goto done;
+            if (p.profile && cta == 0 && threadIdx.x == 0) {
+                const unsigned long long t_r3 = gtimer();
+                ctl->prof[0] += t_r1 - t_r0;
+                ctl->prof[1] += t_r2 - t_r1;
+                ctl->prof[2] += t_r3 - t_r2;
+                ctl->prof[3] += 1;
+            }
             const unsigned long long pub = s.pub;
             if ((pub >> 31) & 1ull) ++rounds;
             nf_next += (long long)(pub & 0x3FFFFFFFull);
@@ -661,7 +674,10 @@ struct PhaseCfg {
     size_t smem = 0;
 };
 
-size_t smem_bytes(int ldq) { return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)ldq * sizeof(uint16_t); }
+size_t smem_bytes(int ldq) {
+    return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)ldq * sizeof(uint16_t) +
+           (size_t)((ldq + 31) / 32) * sizeof(unsigned);
+}
 
 pr_status phase_cfg(PhaseCfg &cfg) {
     static int cached_dev = -1;
@@ -717,7 +733,7 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     const Layout L = make_layout(n_rows, n_cols, cfg.grid);
     if (smem_bytes(L.ldq) > cfg.smem)
         return fail(PR_ERR_INVALID, "pr_assign: n_cols = %d exceeds the shared-memory key copy (max %d)",
-                    n_cols, (int)((cfg.smem - smem_bytes(0)) / sizeof(uint16_t)) & ~7);
+                    n_cols, (int)((cfg.smem - smem_bytes(0)) * 16 / 33) & ~31);
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
         return fail(PR_ERR_WORKSPACE, "pr_assign: workspace NULL, not 256-byte aligned or < %zu bytes",
                     L.total);
@@ -741,6 +757,10 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     const long long K = (long long)floor(1.0 / eps);
     p.phase_cap = ((long long)n_rows * (2 * K + 3)) / (p.T + 1) + 1;
     p.spin_limit = spin_limit_cycles();
+    {
+        const char *pf = getenv("PR_PROFILE");
+        p.profile = (pf && *pf == '1') ? 1 : 0;
+    }
 
     const DeviceInfo &di = device_info();
     k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
