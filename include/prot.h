@@ -97,6 +97,68 @@ pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int
                     int32_t *y_col, double *cost, pr_stats *stats, void *ws, size_t ws_bytes,
                     void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched form: many independent square problems in one persistent launch.  */
+/* ------------------------------------------------------------------------ */
+
+/* Launch shape of the batched solver (0 = default). */
+typedef struct {
+    int32_t threads;     /* threads per solver CTA: 128, 256, 512 or 1024 (0 = 256) */
+    int32_t ctas_per_sm; /* resident solver CTAs per SM, 0 = as many as fit        */
+} pr_batched_tune;
+
+typedef enum { PR_SQEUCLIDEAN = 0, PR_EUCLIDEAN = 1 } pr_metric;
+
+/*
+ * Workspace bytes of pr_assign_batched / pr_assign_batched_points for
+ * n_problems problems of sizes n_host[0..n_problems) (host array); 0 if a
+ * size is outside 1..5000.
+ */
+size_t pr_assign_batched_workspace(int32_t n_problems, const int32_t *n_host);
+
+/*
+ * pr_assign_batched -- pr_assign's method (Sec. 2.2, Eq. 1, completion of
+ * Sec. 2.1) applied to n_problems independent square problems in one
+ * persistent launch: one CTA per problem at a time, problems taken largest
+ * first, all per-problem state in shared memory.  Each problem's result is
+ * bit-identical to pr_assign on that problem alone.
+ *
+ *   C          packed costs in [0,1]: problem i is n_i x n_i row-major at
+ *              element offset sum_{j<i} n_j^2 (rows = the proposing side B)
+ *   n_host     host array of the n_i, 1 <= n_i <= 5000
+ *   row_to_col, col_to_row, y_row, y_col
+ *              packed per problem at offset v_i = sum_{j<i} n_j; indices are
+ *              local to the problem (0..n_i-1), duals in units of eps
+ *   costs      [n_problems] FP64 matching costs in input units
+ *   phases     [n_problems] phases each problem ran
+ *   tune       host, may be NULL (defaults)
+ *   stats      host, may be NULL; totals over all problems; non-NULL syncs
+ * The problem table is copied from host memory with cudaMemcpyAsync, which
+ * waits for work queued earlier on `stream`.
+ */
+pr_status pr_assign_batched(const void *C, pr_dtype dt, int32_t n_problems, const int32_t *n_host,
+                            double eps, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                            int32_t *y_col, double *costs, int64_t *phases,
+                            const pr_batched_tune *tune, pr_stats *stats, void *ws,
+                            size_t ws_bytes, void *stream);
+
+/*
+ * pr_assign_batched_points -- as pr_assign_batched, with the costs of each
+ * problem formed from point sets (Sec. 1 and Sec. 5: cost = distance between
+ * a point of A and a point of B, scaled so the largest cost is 1).  For
+ * problem i, XA and XB hold rows v_i .. v_i + n_i - 1 of (sum n) x dim FP32
+ * arrays; XB are the rows (B), XA the columns (A).  d = sum_k (xb_k - xa_k)^2
+ * in FP32, one IEEE operation at a time in ascending k (PR_EUCLIDEAN: its
+ * IEEE square root); the rounded costs use c = RN32(d / max d).  costs[i] is
+ * the matched distance sum in input units, evaluated in FP64.
+ */
+pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim, pr_metric metric,
+                                   int32_t n_problems, const int32_t *n_host, double eps,
+                                   int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                                   int32_t *y_col, double *costs, int64_t *phases,
+                                   const pr_batched_tune *tune, pr_stats *stats, void *ws,
+                                   size_t ws_bytes, void *stream);
+
 /*
  * Synchronise `stream` and return the device-side status recorded in a
  * workspace by the last call that used it (PR_OK if none).  For callers that

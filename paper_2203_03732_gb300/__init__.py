@@ -5,7 +5,9 @@ Optimal Transport" (arXiv 2203.03732).  The solver runs in the CUDA library
 ``libprot.so`` behind the C ABI of ``include/prot.h``; this package is a thin
 torch-facing wrapper (device memory, streams, argument marshalling).
 
-    assign(C, eps)  -> matching, integer duals (units of eps), cost
+    assign(C, eps)                     one problem
+    assign_batched(C, sizes, eps)      many square problems, one launch
+    assign_batched_points(XA, XB, sizes, eps)   the same with costs from points
 """
 from __future__ import annotations
 
@@ -13,7 +15,7 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["assign", "Workspace", "PrError"]
+__all__ = ["assign", "assign_batched", "assign_batched_points", "Workspace", "PrError"]
 
 PrError = _lib.PrError
 
@@ -106,4 +108,116 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
         res["stats"] = st.as_dict()
     if host_in:
         res = {k: (v.cpu() if hasattr(v, "cpu") else v) for k, v in res.items()}
+    return res
+
+
+def _tune_struct(tune):
+    if tune is None:
+        return None
+    t = _lib.PrBatchedTune()
+    t.threads, t.ctas_per_sm = int(tune[0]), int(tune[1])
+    return ctypes.byref(t)
+
+
+def _batched_outputs(torch, dev, sizes):
+    import numpy as np
+    tot = int(np.sum(sizes))
+    P = len(sizes)
+    return dict(
+        row_to_col=torch.empty(tot, dtype=torch.int32, device=dev),
+        col_to_row=torch.empty(tot, dtype=torch.int32, device=dev),
+        y_row=torch.empty(tot, dtype=torch.int32, device=dev),
+        y_col=torch.empty(tot, dtype=torch.int32, device=dev),
+        costs=torch.empty(P, dtype=torch.float64, device=dev),
+        phases=torch.empty(P, dtype=torch.int64, device=dev),
+    )
+
+
+def _sizes_arg(sizes):
+    import numpy as np
+    n = np.ascontiguousarray(np.asarray(sizes), dtype=np.int32)
+    return n, n.ctypes.data_as(ctypes.c_void_p)
+
+
+def assign_batched(C, sizes, eps: float, *, tune=None, sync: bool = True,
+                   ws: Workspace | None = None, out=None):
+    """Many independent square problems in one persistent launch.
+
+    C: 1-D CUDA tensor (float32/float64) holding the problems' n_i x n_i cost
+    matrices back to back (rows = proposing side), costs in [0, 1].
+    sizes: the n_i (host).  Returns packed row_to_col, col_to_row, y_row,
+    y_col (offset sum_{j<i} n_j, indices local to each problem), costs[P],
+    phases[P] and, when sync, stats (totals).
+    """
+    torch = _torch()
+    L = _lib.load()
+    if not C.is_cuda:
+        raise ValueError("C must be a CUDA tensor")
+    C = C.contiguous()
+    dt = {torch.float64: _lib.PR_F64, torch.float32: _lib.PR_F32}.get(C.dtype)
+    if dt is None:
+        raise TypeError("C must be float32 or float64")
+    n, n_ptr = _sizes_arg(sizes)
+    if C.numel() != int((n.astype("int64") ** 2).sum()):
+        raise ValueError("C does not hold sum n_i^2 elements")
+    dev = C.device
+    need = L.pr_assign_batched_workspace(len(n), n_ptr)
+    if need == 0:
+        raise PrError(_lib.PR_ERR_INVALID, "invalid problem sizes (need 1 <= n_i <= 5000)")
+    wsb = (ws or _workspace(dev)).get(need)
+    out = out or _batched_outputs(torch, dev, n)
+    st = _lib.PrStats()
+    rc = L.pr_assign_batched(C.data_ptr(), dt, len(n), n_ptr, float(eps),
+                             out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
+                             out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["costs"].data_ptr(),
+                             out["phases"].data_ptr(), _tune_struct(tune),
+                             ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
+                             _stream_handle(torch, dev))
+    _lib.check(rc, "pr_assign_batched")
+    res = dict(out)
+    if sync:
+        res["stats"] = st.as_dict()
+    return res
+
+
+def assign_batched_points(XA, XB, sizes, eps: float, *, metric: str = "sqeuclidean", tune=None,
+                          sync: bool = True, ws: Workspace | None = None, out=None):
+    """Batched solve with costs formed from point sets.
+
+    XA, XB: (sum n_i, dim) float32 CUDA tensors; problem i owns rows
+    sum_{j<i} n_j .. + n_i of each; XB are the proposing rows (B), XA the
+    columns (A).  metric: "sqeuclidean" or "euclidean".  Costs are scaled per
+    problem so the largest is 1; reported costs are in input units.
+    """
+    torch = _torch()
+    L = _lib.load()
+    if not (XA.is_cuda and XB.is_cuda):
+        raise ValueError("points must be CUDA tensors")
+    if XA.dtype != torch.float32 or XB.dtype != torch.float32:
+        raise TypeError("points must be float32")
+    XA, XB = XA.contiguous(), XB.contiguous()
+    if XA.shape != XB.shape or XA.dim() != 2:
+        raise ValueError("XA and XB must both be (sum n_i, dim)")
+    m = {"sqeuclidean": _lib.PR_SQEUCLIDEAN, "euclidean": _lib.PR_EUCLIDEAN}[metric]
+    n, n_ptr = _sizes_arg(sizes)
+    if XA.shape[0] != int(n.sum()):
+        raise ValueError("points do not hold sum n_i rows")
+    dev = XA.device
+    need = L.pr_assign_batched_workspace(len(n), n_ptr)
+    if need == 0:
+        raise PrError(_lib.PR_ERR_INVALID, "invalid problem sizes (need 1 <= n_i <= 5000)")
+    wsb = (ws or _workspace(dev)).get(need)
+    out = out or _batched_outputs(torch, dev, n)
+    st = _lib.PrStats()
+    rc = L.pr_assign_batched_points(XA.data_ptr(), XB.data_ptr(), XA.shape[1], m, len(n), n_ptr,
+                                    float(eps), out["row_to_col"].data_ptr(),
+                                    out["col_to_row"].data_ptr(), out["y_row"].data_ptr(),
+                                    out["y_col"].data_ptr(), out["costs"].data_ptr(),
+                                    out["phases"].data_ptr(), _tune_struct(tune),
+                                    ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
+                                    _stream_handle(torch, dev))
+    _lib.check(rc, "pr_assign_batched_points")
+    res = dict(out)
+    if sync:
+        res["stats"] = st.as_dict()
     return res

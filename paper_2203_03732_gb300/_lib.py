@@ -38,6 +38,14 @@ class PrStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PrBatchedTune(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+PR_SQEUCLIDEAN = 0
+PR_EUCLIDEAN = 1
+
+
 class PrError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -58,6 +66,13 @@ SIGNATURES = {
     "pr_assign_workspace": (_sz, [_i32, _i32]),
     "pr_assign": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp,
                                  ctypes.POINTER(PrStats), _vp, _sz, _vp]),
+    "pr_assign_batched_workspace": (_sz, [_i32, _vp]),
+    "pr_assign_batched": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _vp, _dbl, _vp, _vp, _vp, _vp, _vp,
+                                         _vp, ctypes.POINTER(PrBatchedTune), ctypes.POINTER(PrStats),
+                                         _vp, _sz, _vp]),
+    "pr_assign_batched_points": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _i32, _vp, _dbl, _vp, _vp,
+                                                _vp, _vp, _vp, _vp, ctypes.POINTER(PrBatchedTune),
+                                                ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),
     "pr_set_kernel_events": (None, [_vp, _vp]),
     "pr_last_error": (ctypes.c_char_p, []),

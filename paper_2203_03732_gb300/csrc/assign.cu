@@ -37,6 +37,7 @@
 #include <string.h>
 
 #include "prot_internal.cuh"
+#include "scan_common.cuh"
 
 namespace prot {
 namespace {
@@ -47,8 +48,6 @@ constexpr int kUnroll = 8;                // 16-byte loads in flight per lane pe
 constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk (4 KiB)
 constexpr int kListSm = 2048;             // list entries kept in shared memory
 constexpr int kBatch = 256;               // items turned into scan jobs at a time
-constexpr uint16_t kPadCost = 0x7FFF;     // cbar of padding columns
-constexpr uint16_t kPadKey = 0x8000;      // k of padding columns: pad sum 0xFFFF never matches
 constexpr int kMaxGrid = 1023;            // barrier payload field width
 
 // Control block at the start of the workspace.
@@ -108,18 +107,6 @@ struct Params {
     int profile;
 };
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
-__device__ __forceinline__ int row_of(unsigned long long w) { return (int)(0xFFFFFFFFu - (unsigned)w); }
-__device__ __forceinline__ unsigned long long word_of(unsigned R, int b) {
-    return ((unsigned long long)R << 32) | (0xFFFFFFFFu - (unsigned)b);
-}
-
 // ---------------------------------------------------------------------------
 // k_init
 // ---------------------------------------------------------------------------
@@ -143,25 +130,8 @@ __global__ void k_init(Params p, int *match_b) {
 }
 
 // ---------------------------------------------------------------------------
-// k_quantise: Eq. (1) exactly, cbar = largest k with k * eps <= c.
-// An FP32 estimate q of c/eps is within 0.006 of the exact quotient (three
-// roundings of relative size 2^-24 on a quotient <= 32767), so floor(q) is
-// exact whenever q is at least 1/64 away from an integer.  Otherwise the
-// integer is settled with fma(-k, eps, c), whose sign is that of the exact
-// c - k*eps.  No FP64 division runs per element.
+// k_quantise: Eq. (1) exactly (quantise_one), 8 columns per thread.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t quantise_one(double c, double eps, float inv_eps) {
-    const float q = __fmul_rn((float)c, inv_eps);
-    const float kf = floorf(q);
-    const float fr = q - kf;
-    int k = (int)kf;
-    if (!(fr >= 0.015625f && fr <= 0.984375f)) {
-        while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
-        while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
-    }
-    return (uint32_t)k;
-}
-
 template <class T>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
                            double eps, float inv_eps, uint16_t *__restrict__ cb, WsHead *head) {
@@ -205,28 +175,6 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
 // phase nothing is taken; in later rounds a candidate column is skipped when
 // its word carries a tag of an earlier round of this phase.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 ld_nc_na_v4(const void *p) {
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
-    const uint32_t w0 = s.x ^ t2, w1 = s.y ^ t2, w2 = s.z ^ t2, w3 = s.w ^ t2;
-    unsigned m = 0;
-    m |= (w0 & 0xFFFFu) == 0 ? 1u : 0u;
-    m |= (w0 >> 16) == 0 ? 2u : 0u;
-    m |= (w1 & 0xFFFFu) == 0 ? 4u : 0u;
-    m |= (w1 >> 16) == 0 ? 8u : 0u;
-    m |= (w2 & 0xFFFFu) == 0 ? 16u : 0u;
-    m |= (w2 >> 16) == 0 ? 32u : 0u;
-    m |= (w3 & 0xFFFFu) == 0 ? 64u : 0u;
-    m |= (w3 >> 16) == 0 ? 128u : 0u;
-    return m;
-}
-
 // Lowest candidate column in [c0, c0 + kChunk) that is >= start and not in the
 // phase's taken set tk (shared memory; empty in a phase's first round), or -1.
 __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ks,

@@ -1,0 +1,748 @@
+// batched.cu -- many independent assignment problems in one persistent launch.
+//
+// Each CTA pulls problems from a queue in longest-first order (LPT on n) and
+// runs the whole main routine of Sec. 2.2 on one problem with every piece of
+// per-problem state in shared memory: the keys k(A), the proposal words, the
+// row duals, the free-row lists and the proposal lists.  Rounds are separated
+// by __syncthreads() instead of a grid barrier.  Only the rounded cost rows
+// are read from global memory (HBM / L2), one warp per row.
+//
+// Problem i is square (n_i rows and columns).  Packed layouts:
+//   costs   C[c_off_i + b * n_i + a], c_off_i = sum_{j<i} n_j^2 (rows = B)
+//   points  XA[(v_off_i + a) * dim + k], XB[(v_off_i + b) * dim + k]
+//   vectors row_to_col[v_off_i + b] (a column of problem i), v_off_i = sum_{j<i} n_j
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "prot_internal.cuh"
+#include "scan_common.cuh"
+
+namespace prot {
+namespace {
+
+constexpr int kUnroll = 8;
+constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk
+constexpr int kMaxN = 5000;               // largest problem whose state fits shared memory
+
+struct BDesc {
+    long long cb_off;  // element offset of the rounded costs (row stride ldq)
+    long long c_off;   // element offset of the cost matrix (matrix source)
+    long long g_off;   // first 8-column group in the flat quantise index
+    long long cap;     // phase cap
+    int n;
+    int ldq;
+    int v_off;
+    int T;
+};
+
+struct BCtl {
+    WsHead head;
+    unsigned queue;
+    unsigned pad;
+    long long phases;
+    long long rounds;
+    unsigned long long bytes;
+    unsigned long long rows;
+};
+
+struct BLayout {
+    size_t ctl, desc, order, maxbits, cb, total;
+};
+
+BLayout make_blayout(int P, long long cb_elems) {
+    BLayout L;
+    Carver c;
+    L.ctl = c.take<BCtl>(1);
+    L.desc = c.take<BDesc>(P);
+    L.order = c.take<int>(P);
+    L.maxbits = c.take<unsigned>(P);
+    L.cb = c.take<uint16_t>((size_t)cb_elems);
+    L.total = c.total();
+    return L;
+}
+
+struct BParams {
+    BCtl *ctl;
+    const BDesc *desc;
+    const int *order;
+    const unsigned *maxbits;
+    const uint16_t *cb;
+    int nprob;
+    int n_max;
+    int ldq_max;
+    // cost source for the reported costs
+    const void *C;
+    int dt;  // PR_F32 / PR_F64 (matrix source)
+    const float *XA, *XB;
+    int dim, squared, points;
+    // outputs
+    int *row_to_col, *col_to_row, *y_row, *y_col;
+    double *costs;
+    int64_t *phases;
+};
+
+// Flat index g of an 8-column group -> problem (binary search on g_off).
+__device__ __forceinline__ int problem_of(const BDesc *d, int P, long long g) {
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].g_off <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Rounding of the packed matrices (Eq. 1, exact).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict__ d, int P,
+                                long long total_groups, double eps, float inv_eps,
+                                uint16_t *__restrict__ cb, WsHead *head) {
+    bool bad = false;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int i = problem_of(d, P, g);
+        const BDesc D = d[i];
+        const long long lg = g - D.g_off;
+        const int gpr = D.ldq >> 3;
+        const int b = (int)(lg / gpr);
+        const int a0 = (int)(lg - (long long)b * gpr) << 3;
+        const T *row = C + D.c_off + (long long)b * D.n;
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t h[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int a = a0 + 2 * j + k;
+                if (a < D.n) {
+                    const double c = (double)row[a];
+                    if (!(c >= 0.0 && c <= 1.0)) {
+                        bad = true;
+                        h[k] = 0;
+                    } else {
+                        h[k] = quantise_one(c, eps, inv_eps);
+                    }
+                } else {
+                    h[k] = kPadCost;
+                }
+            }
+            w[j] = h[0] | (h[1] << 16);
+        }
+        *reinterpret_cast<uint4 *>(cb + D.cb_off + (long long)b * D.ldq + a0) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (bad) record_error(head, PR_ERR_INVALID);
+}
+
+// ---------------------------------------------------------------------------
+// Costs from points.  d(b,a) = sum_k (xb_k - xa_k)^2 in FP32, one IEEE
+// operation at a time in ascending k (no contraction); Euclidean takes the
+// IEEE square root.  c = RN32(d / max d) so the largest cost is 1 (Sec. 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dist_f32(const float *xb, const float *xa, int dim, int squared) {
+    float acc = 0.0f;
+    for (int k = 0; k < dim; ++k) {
+        const float t = __fsub_rn(xb[k], xa[k]);
+        const float sq = __fmul_rn(t, t);
+        acc = k == 0 ? sq : __fadd_rn(acc, sq);
+    }
+    return squared ? acc : __fsqrt_rn(acc);
+}
+
+__device__ __forceinline__ double dist_f64(const float *xb, const float *xa, int dim, int squared) {
+    double acc = 0.0;
+    for (int k = 0; k < dim; ++k) {
+        const double t = __dsub_rn((double)xb[k], (double)xa[k]);
+        const double sq = __dmul_rn(t, t);
+        acc = k == 0 ? sq : __dadd_rn(acc, sq);
+    }
+    return squared ? acc : __dsqrt_rn(acc);
+}
+
+__global__ void k_bpoints_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
+                              int squared, const BDesc *__restrict__ d, int P,
+                              long long total_groups, unsigned *maxbits) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int i = problem_of(d, P, g);
+        const BDesc D = d[i];
+        const long long lg = g - D.g_off;
+        const int gpr = D.ldq >> 3;
+        const int b = (int)(lg / gpr);
+        const int a0 = (int)(lg - (long long)b * gpr) << 3;
+        const float *xb = XB + (long long)(D.v_off + b) * dim;
+        float m = 0.0f;
+        for (int j = 0; j < 8 && a0 + j < D.n; ++j)
+            m = fmaxf(m, dist_f32(xb, XA + (long long)(D.v_off + a0 + j) * dim, dim, squared));
+        // non-negative floats order like their bit patterns; one atomic per
+        // group of lanes working on the same problem
+        const unsigned active = __activemask();
+        const unsigned same = __match_any_sync(active, i);
+        const unsigned mx = __reduce_max_sync(same, __float_as_uint(m));
+        if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(maxbits + i, mx);
+    }
+}
+
+__global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
+                                int squared, const BDesc *__restrict__ d, int P,
+                                long long total_groups, const unsigned *__restrict__ maxbits,
+                                double eps, float inv_eps, uint16_t *__restrict__ cb) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int i = problem_of(d, P, g);
+        const BDesc D = d[i];
+        const long long lg = g - D.g_off;
+        const int gpr = D.ldq >> 3;
+        const int b = (int)(lg / gpr);
+        const int a0 = (int)(lg - (long long)b * gpr) << 3;
+        const float M = __uint_as_float(maxbits[i]);
+        const float *xb = XB + (long long)(D.v_off + b) * dim;
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int a = a0 + j;
+            if (a < D.n) {
+                const float dd = dist_f32(xb, XA + (long long)(D.v_off + a) * dim, dim, squared);
+                const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
+                h[j] = quantise_one((double)c, eps, inv_eps);
+            } else {
+                h[j] = kPadCost;
+            }
+        }
+        *reinterpret_cast<uint4 *>(cb + D.cb_off + (long long)b * D.ldq + a0) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The per-problem solver.
+// ---------------------------------------------------------------------------
+struct BShared {
+    int nfl[2], nql[2], nwon;
+    int had_prop, nonfirst;
+    int cur_problem;
+    int total;
+    int warp_tot[32];
+    unsigned long long bytes, rows;
+};
+
+// Lowest column a >= start of the row with cbar + k(a) == tgt whose word does
+// not carry a tag in [Rps, R) (taken earlier in this phase), or -1.
+__device__ __forceinline__ int warp_scan_row(const uint16_t *__restrict__ row, const uint16_t *ks,
+                                             const unsigned long long *pw, int start, int ldq,
+                                             uint32_t tgt, unsigned R, unsigned Rps, int lane,
+                                             unsigned long long &bytes) {
+    const uint32_t t2 = tgt | (tgt << 16);
+    const bool check_taken = R > Rps;
+    for (int c0 = start & ~7; c0 < ldq; c0 += kChunk) {
+        uint4 sv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = c0 + u * 256 + lane * 8;
+            if (idx < ldq) {
+                const uint4 c = ld_nc_na_v4(row + idx);
+                const uint4 k = *reinterpret_cast<const uint4 *>(ks + idx);
+                sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
+            } else {
+                sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+            }
+        }
+        bytes += 2ull * (unsigned long long)min(kChunk, ldq - c0);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = c0 + u * 256 + lane * 8;
+            unsigned m = eq_mask(sv[u], t2);
+            const int lo = start - idx;
+            if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+            for (;;) {
+                const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
+                if (any == 0) break;
+                const int L = __ffs(any) - 1;
+                const int a = __shfl_sync(0xFFFFFFFFu, idx + __ffs(m) - 1, L);
+                bool taken = false;
+                if (check_taken) {
+                    const unsigned t = tag_of(pw[a]);
+                    taken = t >= Rps && t < R;
+                }
+                if (!taken) return a;
+                if (lane == L) m &= m - 1;
+            }
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int block_scan_excl(int flag, BShared &s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, flag);
+    const int within = __popc(bal & ((1u << lane) - 1));
+    if (lane == 0) s.warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < nw ? s.warp_tot[lane] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < nw) s.warp_tot[lane] = x - v;
+        if (lane == 31) s.total = x;
+    }
+    __syncthreads();
+    const int r = s.warp_tot[warp] + within;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_bsolve(BParams p) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ BShared s;
+    const int nmax = p.n_max;
+    unsigned long long *pw = reinterpret_cast<unsigned long long *>(dyn);
+    int *yb = reinterpret_cast<int *>(pw + nmax);
+    int *fl0 = yb + nmax;
+    int *fl1 = fl0 + nmax;
+    int2 *ql0 = reinterpret_cast<int2 *>(fl1 + nmax);
+    int2 *ql1 = ql0 + nmax;
+    int *won = reinterpret_cast<int *>(ql1 + nmax);
+    uint16_t *ks = reinterpret_cast<uint16_t *>(won + nmax);
+    int *fl[2] = {fl0, fl1};
+    int2 *ql[2] = {ql0, ql1};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    if (threadIdx.x == 0) s.bytes = s.rows = 0;
+    long long my_phases = 0, my_rounds = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int t = (int)atomicAdd(&p.ctl->queue, 1u);
+            if (ld_relaxed_s32(&p.ctl->head.abort)) t = p.nprob;  // stop after an error
+            s.cur_problem = t;
+        }
+        __syncthreads();
+        const int t = s.cur_problem;
+        __syncthreads();  // every thread has read cur_problem before it changes
+        if (t >= p.nprob) break;
+        const int pi = p.order[t];
+        const BDesc D = p.desc[pi];
+        const int n = D.n, ldq = D.ldq;
+        const uint16_t *cb = p.cb + D.cb_off;
+
+        // Initialisation (Sec. 2.2): y(b) = eps, y(a) = 0, M empty, B' = B.
+        for (int a = threadIdx.x; a < ldq; a += blockDim.x) ks[a] = a < n ? 0 : kPadKey;
+        for (int a = threadIdx.x; a < n; a += blockDim.x) pw[a] = word_of(0, -1);
+        for (int b = threadIdx.x; b < n; b += blockDim.x) {
+            yb[b] = 1;
+            fl0[b] = b;
+        }
+        if (threadIdx.x == 0) {
+            s.nfl[0] = n;
+            s.nfl[1] = 0;
+        }
+        __syncthreads();
+
+        unsigned R = 0;
+        long long phases = 0;
+        int cur = 0, qcur = 0;
+        bool failed = false;
+        for (;;) {
+            const int nf = s.nfl[cur];
+            if (nf <= D.T) break;
+            if (phases >= D.cap) {
+                failed = true;
+                break;
+            }
+            ++phases;
+            const unsigned Rps = R + 1;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s.nfl[cur ^ 1] = 0;
+                s.nwon = 0;
+            }
+            bool first = true;
+            for (;;) {
+                ++R;
+                if (threadIdx.x == 0) {
+                    s.nql[qcur] = 0;
+                    s.had_prop = 0;
+                    s.nonfirst = 0;
+                }
+                __syncthreads();
+                const int items = first ? nf : s.nql[qcur ^ 1];
+                unsigned long long my_bytes = 0;
+                for (int it = warp; it < items; it += nwarps) {
+                    int b, start = 0;
+                    if (first) {
+                        b = fl[cur][it];
+                    } else {
+                        const int2 q = ql[qcur ^ 1][it];
+                        b = q.x;
+                        if (row_of(pw[q.y]) == b) continue;  // won: matched
+                        start = q.y + 1;                     // lost: resume after a
+                    }
+                    const uint32_t tgt = (uint32_t)(yb[b] - 1);
+                    const int a = warp_scan_row(cb + (long long)b * ldq, ks, pw, start, ldq, tgt, R,
+                                                Rps, lane, my_bytes);
+                    if (lane == 0) {
+                        if (a >= 0) {
+                            const unsigned long long old = atomicMax(pw + a, word_of(R, b));
+                            if (tag_of(old) < Rps) {
+                                // first proposal: a is won this round (step III a
+                                // at the phase end), its partner is evicted (II)
+                                won[atomicAdd(&s.nwon, 1)] = a;
+                                const int partner = row_of(old);
+                                if (partner >= 0) fl[cur ^ 1][atomicAdd(&s.nfl[cur ^ 1], 1)] = partner;
+                            } else {
+                                s.nonfirst = 1;
+                            }
+                            const int j = atomicAdd(&s.nql[qcur], 1);
+                            ql[qcur][j] = make_int2(b, a);
+                            s.had_prop = 1;
+                        } else {
+                            yb[b] += 1;  // step (III b): relabel
+                            fl[cur ^ 1][atomicAdd(&s.nfl[cur ^ 1], 1)] = b;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (my_bytes) atomicAdd(&s.bytes, my_bytes);
+                }
+                __syncthreads();
+                const bool had = s.had_prop != 0, contested = s.nonfirst != 0;
+                if (threadIdx.x == 0) s.rows += (unsigned long long)items;
+                __syncthreads();
+                if (had) ++my_rounds;
+                qcur ^= 1;
+                first = false;
+                if (!contested) break;
+            }
+            // step (III a): y(a) -= eps for the columns won in this phase
+            for (int i = threadIdx.x; i < s.nwon; i += blockDim.x) ks[won[i]] += 1;
+            cur ^= 1;
+            __syncthreads();
+        }
+        my_phases += phases;
+        if (failed) {
+            if (threadIdx.x == 0) record_error(&p.ctl->head, PR_ERR_NO_CONVERGENCE);
+            __syncthreads();
+            continue;
+        }
+
+        // Matching out of the words, completion, duals, cost.
+        int *mb = fl0, *ma = fl1;
+        for (int b = threadIdx.x; b < n; b += blockDim.x) mb[b] = -1;
+        __syncthreads();
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            const unsigned long long w = pw[a];
+            const int b = tag_of(w) > 0 ? row_of(w) : -1;
+            ma[a] = b;
+            if (b >= 0) mb[b] = a;
+        }
+        __syncthreads();
+        // k-th free row (ascending) with the k-th free column (ascending)
+        int *free_b = reinterpret_cast<int *>(ql0);
+        int *free_a = free_b + n;
+        int nfb = 0;
+        for (int base = 0; base < n; base += blockDim.x) {
+            const int b = base + threadIdx.x;
+            const int f = (b < n && mb[b] < 0) ? 1 : 0;
+            const int pos = block_scan_excl(f, s);
+            if (f) free_b[nfb + pos] = b;
+            nfb += s.total;
+            __syncthreads();
+        }
+        int nfa = 0;
+        for (int base = 0; base < n && nfa < nfb; base += blockDim.x) {
+            const int a = base + threadIdx.x;
+            const int f = (a < n && ma[a] < 0) ? 1 : 0;
+            const int pos = block_scan_excl(f, s);
+            if (f && nfa + pos < nfb) free_a[nfa + pos] = a;
+            nfa += s.total;
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < nfb; k += blockDim.x) {
+            mb[free_b[k]] = free_a[k];
+            ma[free_a[k]] = free_b[k];
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < n; b += blockDim.x) {
+            p.row_to_col[D.v_off + b] = mb[b];
+            p.y_row[D.v_off + b] = yb[b];
+            double c;
+            if (p.points) {
+                c = dist_f64(p.XB + (long long)(D.v_off + b) * p.dim,
+                             p.XA + (long long)(D.v_off + mb[b]) * p.dim, p.dim, p.squared);
+            } else if (p.dt == PR_F64) {
+                c = reinterpret_cast<const double *>(p.C)[D.c_off + (long long)b * n + mb[b]];
+            } else {
+                c = (double)reinterpret_cast<const float *>(p.C)[D.c_off + (long long)b * n + mb[b]];
+            }
+            acc = __dadd_rn(acc, c);
+        }
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            p.col_to_row[D.v_off + a] = ma[a];
+            p.y_col[D.v_off + a] = -(int)ks[a];
+        }
+        // fixed-order tree reduction of the per-thread partial sums
+        double *part = reinterpret_cast<double *>(pw);
+        __syncthreads();
+        part[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            p.costs[pi] = part[0];
+            p.phases[pi] = phases;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd((unsigned long long *)&p.ctl->phases, (unsigned long long)my_phases);
+        atomicAdd((unsigned long long *)&p.ctl->rounds, (unsigned long long)my_rounds);
+        atomicAdd(&p.ctl->bytes, s.bytes);
+        atomicAdd(&p.ctl->rows, s.rows);
+    }
+}
+
+size_t bsolve_smem(int n_max, int ldq_max, int threads) {
+    // pw (8) + yb (4) + fl 2x(4) + ql 2x(8) + won (4) per row, keys 2 per column;
+    // the cost reduction reuses the front as one double per thread
+    const size_t state = (size_t)n_max * (8 + 4 + 8 + 16 + 4) + (size_t)ldq_max * 2;
+    const size_t red = (size_t)threads * sizeof(double);
+    return state > red ? state : red;
+}
+
+__global__ void k_binit(BCtl *ctl, unsigned *maxbits, int P) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        memset(ctl, 0, sizeof(BCtl));
+        ctl->head.magic = kWsMagic;
+    }
+    for (int i = t; i < P; i += gridDim.x * blockDim.x) maxbits[i] = 0;
+}
+
+struct Plan {
+    std::vector<BDesc> desc;
+    std::vector<int> order;
+    long long cb_elems = 0, groups = 0, c_elems = 0;
+    int n_max = 0, ldq_max = 0, v_total = 0;
+};
+
+pr_status make_plan(int P, const int32_t *n_host, double eps, Plan &pl) {
+    if (P < 1) return fail(PR_ERR_INVALID, "batched: n_problems must be >= 1");
+    if (!n_host) return fail(PR_ERR_INVALID, "batched: NULL size array");
+    pl.desc.resize(P);
+    long long cb = 0, g = 0, c = 0;
+    long long v = 0;
+    const long long K = eps > 0 ? (long long)floor(1.0 / eps) : 0;
+    for (int i = 0; i < P; ++i) {
+        const int n = n_host[i];
+        if (n < 1 || n > kMaxN) return fail(PR_ERR_INVALID, "batched: problem %d has n = %d (need 1..%d)", i, n, kMaxN);
+        BDesc &d = pl.desc[i];
+        d.n = n;
+        d.ldq = (n + 7) & ~7;
+        d.cb_off = cb;
+        d.c_off = c;
+        d.g_off = g;
+        d.v_off = (int)v;
+        d.T = (int)floor(eps * (double)n);
+        d.cap = ((long long)n * (2 * K + 3)) / (d.T + 1) + 1;
+        cb += (long long)n * d.ldq;
+        c += (long long)n * n;
+        g += (long long)n * (d.ldq >> 3);
+        v += n;
+        pl.n_max = std::max(pl.n_max, n);
+        pl.ldq_max = std::max(pl.ldq_max, d.ldq);
+    }
+    if (v > (1ll << 30)) return fail(PR_ERR_INVALID, "batched: too many rows in total");
+    pl.cb_elems = cb;
+    pl.groups = g;
+    pl.c_elems = c;
+    pl.v_total = (int)v;
+    pl.order.resize(P);
+    std::iota(pl.order.begin(), pl.order.end(), 0);
+    // longest processing time first: larger problems start first
+    std::stable_sort(pl.order.begin(), pl.order.end(),
+                     [&](int a, int b) { return pl.desc[a].n > pl.desc[b].n; });
+    return PR_OK;
+}
+
+struct Source {
+    const void *C = nullptr;
+    pr_dtype dt = PR_F64;
+    const float *XA = nullptr, *XB = nullptr;
+    int dim = 0;
+    int squared = 1;
+    bool points = false;
+};
+
+pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, double eps,
+                      int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
+                      double *costs, int64_t *phases, const pr_batched_tune *tune, pr_stats *stats,
+                      void *ws, size_t ws_bytes, void *stream) {
+    if (!row_to_col || !col_to_row || !y_row || !y_col || !costs || !phases)
+        return fail(PR_ERR_INVALID, "batched: NULL output pointer");
+    if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
+        return fail(PR_ERR_INVALID, "batched: need 0 < eps < 1 and floor(1/eps) <= 32766");
+    Plan pl;
+    pr_status rc = make_plan(P, n_host, eps, pl);
+    if (rc != PR_OK) return rc;
+    const BLayout L = make_blayout(P, pl.cb_elems);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
+        return fail(PR_ERR_WORKSPACE, "batched: workspace NULL, not 256-byte aligned or < %zu bytes", L.total);
+    int threads = 256, per_sm_want = 0;
+    if (tune) {
+        if (tune->threads) threads = tune->threads;
+        per_sm_want = tune->ctas_per_sm;
+    }
+    if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+        return fail(PR_ERR_INVALID, "batched: threads must be 128, 256, 512 or 1024");
+    if (per_sm_want < 0) return fail(PR_ERR_INVALID, "batched: ctas_per_sm must be >= 0");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    BCtl *ctl = (BCtl *)(w + L.ctl);
+    BDesc *d_desc = (BDesc *)(w + L.desc);
+    int *d_order = (int *)(w + L.order);
+    unsigned *d_max = (unsigned *)(w + L.maxbits);
+    uint16_t *d_cb = (uint16_t *)(w + L.cb);
+    const DeviceInfo &di = device_info();
+
+    k_binit<<<(P + 255) / 256, 256, 0, st>>>(ctl, d_max, P);
+    PR_CUDA(cudaGetLastError());
+    // problem table: copied from pageable host memory (waits for earlier work
+    // on the stream; the host vectors may be freed on return)
+    PR_CUDA(cudaMemcpyAsync(d_desc, pl.desc.data(), sizeof(BDesc) * P, cudaMemcpyHostToDevice, st));
+    PR_CUDA(cudaMemcpyAsync(d_order, pl.order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+
+    const float inv_eps = (float)(1.0 / eps);
+    const long long want = pl.groups / 256 + 1;
+    const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
+    if (src.points) {
+        k_bpoints_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups, d_max);
+        PR_CUDA(cudaGetLastError());
+        k_bpoints_quant<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups,
+                                               d_max, eps, inv_eps, d_cb);
+    } else if (src.dt == PR_F64) {
+        k_bquant_matrix<double><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, eps,
+                                                       inv_eps, d_cb, &ctl->head);
+    } else {
+        k_bquant_matrix<float><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, eps, inv_eps,
+                                                      d_cb, &ctl->head);
+    }
+    PR_CUDA(cudaGetLastError());
+
+    const size_t smem = bsolve_smem(pl.n_max, pl.ldq_max, threads);
+    if (smem > (size_t)di.max_smem_optin)
+        return fail(PR_ERR_INVALID, "batched: problem of n = %d does not fit shared memory", pl.n_max);
+    PR_CUDA(cudaFuncSetAttribute(k_bsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bsolve, threads, smem));
+    if (per_sm < 1) return fail(PR_ERR_INVALID, "batched: solver CTA does not fit an SM");
+    if (per_sm_want > 0 && per_sm_want < per_sm) per_sm = per_sm_want;
+    int grid = di.sms * per_sm;
+    if (grid > P) grid = P;
+
+    BParams bp;
+    bp.ctl = ctl;
+    bp.desc = d_desc;
+    bp.order = d_order;
+    bp.maxbits = d_max;
+    bp.cb = d_cb;
+    bp.nprob = P;
+    bp.n_max = pl.n_max;
+    bp.ldq_max = pl.ldq_max;
+    bp.C = src.C;
+    bp.dt = src.dt;
+    bp.XA = src.XA;
+    bp.XB = src.XB;
+    bp.dim = src.dim;
+    bp.squared = src.squared;
+    bp.points = src.points ? 1 : 0;
+    bp.row_to_col = row_to_col;
+    bp.col_to_row = col_to_row;
+    bp.y_row = y_row;
+    bp.y_col = y_col;
+    bp.costs = costs;
+    bp.phases = phases;
+    cudaEvent_t ev0, ev1;
+    kernel_events(&ev0, &ev1);
+    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev0, st));
+    k_bsolve<<<grid, threads, smem, st>>>(bp);
+    PR_CUDA(cudaGetLastError());
+    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
+
+    if (stats) {
+        BCtl h;
+        PR_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        stats->phases = h.phases;
+        stats->rounds = h.rounds;
+        stats->bytes_scanned = (int64_t)h.bytes;
+        stats->rows_scanned = (int64_t)h.rows;
+        stats->free_at_stop = 0;
+        stats->threshold = 0;
+        if (h.head.err != 0)
+            return fail((pr_status)h.head.err, "batched: device reported %s", pr_status_string((pr_status)h.head.err));
+    }
+    return PR_OK;
+}
+
+}  // namespace
+}  // namespace prot
+
+using namespace prot;
+
+extern "C" size_t pr_assign_batched_workspace(int32_t n_problems, const int32_t *n_host) {
+    Plan pl;
+    if (make_plan(n_problems, n_host, 0.5, pl) != PR_OK) return 0;
+    return make_blayout(n_problems, pl.cb_elems).total;
+}
+
+extern "C" pr_status pr_assign_batched(const void *C, pr_dtype dt, int32_t n_problems,
+                                       const int32_t *n_host, double eps, int32_t *row_to_col,
+                                       int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
+                                       double *costs, int64_t *phases, const pr_batched_tune *tune,
+                                       pr_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+    if (!C) return fail(PR_ERR_INVALID, "pr_assign_batched: NULL cost pointer");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_batched: bad dtype");
+    Source src;
+    src.C = C;
+    src.dt = dt;
+    return run_batched(src, n_problems, n_host, eps, row_to_col, col_to_row, y_row, y_col, costs,
+                       phases, tune, stats, ws, ws_bytes, stream);
+}
+
+extern "C" pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim,
+                                              pr_metric metric, int32_t n_problems,
+                                              const int32_t *n_host, double eps,
+                                              int32_t *row_to_col, int32_t *col_to_row,
+                                              int32_t *y_row, int32_t *y_col, double *costs,
+                                              int64_t *phases, const pr_batched_tune *tune,
+                                              pr_stats *stats, void *ws, size_t ws_bytes,
+                                              void *stream) {
+    if (!XA || !XB) return fail(PR_ERR_INVALID, "pr_assign_batched_points: NULL point pointer");
+    if (dim < 1 || dim > 4096) return fail(PR_ERR_INVALID, "pr_assign_batched_points: need 1 <= dim <= 4096");
+    if (metric != PR_SQEUCLIDEAN && metric != PR_EUCLIDEAN)
+        return fail(PR_ERR_INVALID, "pr_assign_batched_points: bad metric");
+    Source src;
+    src.XA = XA;
+    src.XB = XB;
+    src.dim = dim;
+    src.squared = metric == PR_SQEUCLIDEAN ? 1 : 0;
+    src.points = true;
+    return run_batched(src, n_problems, n_host, eps, row_to_col, col_to_row, y_row, y_col, costs,
+                       phases, tune, stats, ws, ws_bytes, stream);
+}
