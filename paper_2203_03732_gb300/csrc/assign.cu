@@ -53,8 +53,7 @@ constexpr int kMaxGrid = 1023;            // barrier payload field width
 // Control block at the start of the workspace.
 struct Ctl {
     WsHead head;
-    unsigned long long bar_acc;  // barrier arrivals + payload (see grid_sync)
-    unsigned long long bar_pub;  // (generation << 32) | published payload
+    unsigned long long bar_slot[4];  // barrier h accumulates arrivals + payload in slot h % 4
     int free_at_stop;
     int pad0;
     long long phases;
@@ -62,8 +61,10 @@ struct Ctl {
     unsigned long long bytes;
     unsigned long long rows;
     // PR_PROFILE=1: CTA 0's %globaltimer split of the rounds (ns): round
-    // start (bitmaps, keys), items + scans + proposals, barrier; round count.
-    unsigned long long prof[4];
+    // start (bitmaps, keys), items + scans + proposals, barrier; round count;
+    // summed over rounds: the slowest CTA's work time and largest item count.
+    unsigned long long prof[6];
+    unsigned long long prof_slot[2][2];  // per round parity: max work ns, max items
 };
 
 struct Layout {
@@ -253,53 +254,45 @@ __device__ __forceinline__ int2 ql_get(const Smem &s, const Lists &g, int which,
     return i < kListSm ? s.ql[which][i] : g.ql[which][i - kListSm];
 }
 
-// Grid barrier carrying a payload: each CTA adds
+// Grid barrier carrying a payload.  Barrier h adds, for each CTA,
 //   1 (arrival) | had_prop << 10 | nonfirst << 20 | nf_delta << 40
-// (had_prop, nonfirst in {0,1}; nf_delta < 2^24) to one 64-bit accumulator.
-// The last arrival resets it and publishes (gen << 32) | (P>0) << 31 |
-// (L>0) << 30 | sum(nf_delta) with a release store; the others spin (bounded)
-// on the published word.  Returns false when the kernel must stop.
+// (had_prop, nonfirst in {0,1}; nf_delta < 2^24; at most 1023 CTAs) to slot
+// h % 4 with one release reduction, then spins (bounded) with acquire loads
+// until the slot's arrival field reaches the grid size; the slot then holds
+// the totals.  CTA 0 zeroes slot (h + 2) % 4 during round h: every CTA read
+// it before arriving at barrier h - 1, and it is reused by barrier h + 2.
+// Returns false when the kernel must stop.
 __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsigned G,
                                           long long limit, unsigned long long mine) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g = gen + 1;
-        __threadfence();
-        const unsigned long long old = atomicAdd(&ctl->bar_acc, mine);
-        unsigned long long pub = 0;
-        if ((old & 1023ull) == (unsigned long long)(G - 1)) {
-            const unsigned long long tot = old + mine;
-            const unsigned long long P = (tot >> 10) & 1023ull;
-            const unsigned long long L = (tot >> 20) & 1023ull;
-            const unsigned long long nf = (tot >> 40) & 0xFFFFFFull;
-            ctl->bar_acc = 0;
-            pub = ((unsigned long long)g << 32) | ((P ? 1ull : 0ull) << 31) |
-                  ((L ? 1ull : 0ull) << 30) | nf;
-            __threadfence();
-            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&ctl->bar_pub), "l"(pub)
-                         : "memory");
-        } else {
-            const long long t0 = clock64();
-            for (;;) {
-                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
-                             : "=l"(pub)
-                             : "l"(&ctl->bar_pub)
-                             : "memory");
-                if ((unsigned)(pub >> 32) == g) break;
-                if (ld_relaxed_s32(&ctl->head.abort)) break;
-                if (clock64() - t0 > limit) {
-                    record_error(&ctl->head, PR_ERR_TIMEOUT);
-                    break;
-                }
+        const unsigned h = gen + 1;
+        unsigned long long *slot = &ctl->bar_slot[h & 3];
+        if (blockIdx.x == 0) ctl->bar_slot[(h + 2) & 3] = 0;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(slot), "l"(mine) : "memory");
+        unsigned long long v = 0;
+        const long long t0 = clock64();
+        bool ok = true;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(slot) : "memory");
+            if ((v & 1023ull) == (unsigned long long)G) break;
+            if (ld_relaxed_s32(&ctl->head.abort)) {
+                ok = false;
+                break;
+            }
+            if (clock64() - t0 > limit) {
+                record_error(&ctl->head, PR_ERR_TIMEOUT);
+                ok = false;
+                break;
             }
         }
-        __threadfence();
-        s.pub = pub;
-        s.err = ld_relaxed_s32(&ctl->head.abort);
+        const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
+        s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
+        s.err = ok ? 0 : 1;
     }
     __syncthreads();
     gen += 1;
-    return s.err == 0 && (unsigned)(s.pub >> 32) == gen;
+    return s.err == 0;
 }
 
 // Scan queued jobs rows_per_group rows at a time with warps_per_row warps per
@@ -486,6 +479,15 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                                             ((unsigned long long)s.nonfirst << 20) |
                                             ((unsigned long long)s.nf_delta << 40);
             const unsigned long long t_r2 = p.profile ? gtimer() : 0;
+            if (p.profile && threadIdx.x == 0) {
+                atomicMax(&ctl->prof_slot[R & 1][0], t_r2 - t_r1);
+                atomicMax(&ctl->prof_slot[R & 1][1], (unsigned long long)nitems);
+                if (cta == 0) {
+                    // read after round R - 1; written again only after this barrier
+                    ctl->prof_slot[(R + 1) & 1][0] = 0;
+                    ctl->prof_slot[(R + 1) & 1][1] = 0;
+                }
+            }
             if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine)) goto done;
             if (p.profile && cta == 0 && threadIdx.x == 0) {
                 const unsigned long long t_r3 = gtimer();
@@ -493,6 +495,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 ctl->prof[1] += t_r2 - t_r1;
                 ctl->prof[2] += t_r3 - t_r2;
                 ctl->prof[3] += 1;
+                ctl->prof[4] += ctl->prof_slot[R & 1][0];
+                ctl->prof[5] += ctl->prof_slot[R & 1][1];
             }
             const unsigned long long pub = s.pub;
             if ((pub >> 31) & 1ull) ++rounds;

@@ -304,7 +304,8 @@ __device__ __forceinline__ int block_scan_excl(int flag, BShared &s) {
     return r;
 }
 
-__global__ void k_bsolve(BParams p) {
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_bsolve(BParams p) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ BShared s;
     const int nmax = p.n_max;
@@ -647,9 +648,13 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     const size_t smem = bsolve_smem(pl.n_max, pl.ldq_max, threads);
     if (smem > (size_t)di.max_smem_optin)
         return fail(PR_ERR_INVALID, "batched: problem of n = %d does not fit shared memory", pl.n_max);
-    PR_CUDA(cudaFuncSetAttribute(k_bsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const void *kern = threads == 128   ? (const void *)k_bsolve<128>
+                       : threads == 256 ? (const void *)k_bsolve<256>
+                       : threads == 512 ? (const void *)k_bsolve<512>
+                                        : (const void *)k_bsolve<1024>;
+    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bsolve, threads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return fail(PR_ERR_INVALID, "batched: solver CTA does not fit an SM");
     if (per_sm_want > 0 && per_sm_want < per_sm) per_sm = per_sm_want;
     int grid = di.sms * per_sm;
@@ -680,8 +685,10 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     cudaEvent_t ev0, ev1;
     kernel_events(&ev0, &ev1);
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev0, st));
-    k_bsolve<<<grid, threads, smem, st>>>(bp);
-    PR_CUDA(cudaGetLastError());
+    {
+        void *args[] = {(void *)&bp};
+        PR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, smem, st));
+    }
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
 
     if (stats) {
