@@ -159,6 +159,32 @@ pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim
                                    const pr_batched_tune *tune, pr_stats *stats, void *ws,
                                    size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Differentiation of the assignment loss.                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * pr_assign_backward -- gradient of the squared-Euclidean assignment loss
+ *   L_p = (1/n) sum_i |x_i - y_sigma(i)|^2
+ * for `batch` pairs of point clouds with the plans sigma_p held fixed (the
+ * plan of Sec. 2.2 is piecewise constant in the coordinates, so this is the
+ * gradient wherever the plan is locally unique; the paper has no backward
+ * pass, this is the envelope rule applied to its output).
+ *
+ *   row_to_col [batch][n] completed plans (permutations), e.g. the packed
+ *              output of pr_assign_batched_points on the pairs
+ *   X, Y       [batch][n][dim] FP32 rows (B) and columns (A) of each pair
+ *   grad_cost  [batch] incoming gradient of each L_p
+ *   grad_X     [batch][n][dim] out: g * 2 (x_i - y_sigma(i)) / n
+ *   grad_Y     [batch][n][dim] out: minus that, at row sigma(i)
+ *   grad_C     [batch][n][n] out or NULL: g / n on matched entries, else 0
+ * Each value is formed in FP64 as ((x - y) * 2) / n * g and rounded once.
+ * Asynchronous; the plans must be permutations (not checked on the device).
+ */
+pr_status pr_assign_backward(const int32_t *row_to_col, const float *X, const float *Y,
+                             int32_t batch, int32_t n, int32_t dim, const float *grad_cost,
+                             float *grad_X, float *grad_Y, float *grad_C, void *stream);
+
 /*
  * Synchronise `stream` and return the device-side status recorded in a
  * workspace by the last call that used it (PR_OK if none).  For callers that

@@ -8,6 +8,7 @@ torch-facing wrapper (device memory, streams, argument marshalling).
     assign(C, eps)                     one problem
     assign_batched(C, sizes, eps)      many square problems, one launch
     assign_batched_points(XA, XB, sizes, eps)   the same with costs from points
+    assignment_loss(X, Y, eps)         differentiable mean matched squared distance
 """
 from __future__ import annotations
 
@@ -15,7 +16,8 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["assign", "assign_batched", "assign_batched_points", "Workspace", "PrError"]
+__all__ = ["assign", "assign_batched", "assign_batched_points", "assign_backward",
+           "assignment_loss", "AssignLoss", "Workspace", "PrError"]
 
 PrError = _lib.PrError
 
@@ -221,3 +223,71 @@ def assign_batched_points(XA, XB, sizes, eps: float, *, metric: str = "sqeuclide
     if sync:
         res["stats"] = st.as_dict()
     return res
+
+
+def assign_backward(row_to_col, X, Y, grad_cost, *, grad_C: bool = False):
+    """Gradients of L_p = (1/n) sum_i |x_i - y_sigma(i)|^2 for (batch, n, dim)
+    FP32 CUDA tensors X (rows) and Y (columns), plans row_to_col (batch*n) and
+    incoming gradients grad_cost (batch,).  Returns (grad_X, grad_Y[, grad_C])."""
+    torch = _torch()
+    L = _lib.load()
+    B, n, d = X.shape
+    X, Y = X.contiguous(), Y.contiguous()
+    g = grad_cost.contiguous().to(torch.float32)
+    r2c = row_to_col.contiguous()
+    gX = torch.empty_like(X)
+    gY = torch.empty_like(Y)
+    gC = torch.empty((B, n, n), dtype=torch.float32, device=X.device) if grad_C else None
+    rc = L.pr_assign_backward(r2c.data_ptr(), X.data_ptr(), Y.data_ptr(), B, n, d, g.data_ptr(),
+                              gX.data_ptr(), gY.data_ptr(), gC.data_ptr() if grad_C else None,
+                              _stream_handle(torch, X.device))
+    _lib.check(rc, "pr_assign_backward")
+    return (gX, gY, gC) if grad_C else (gX, gY)
+
+
+def _assign_loss_function():
+    torch = _torch()
+
+    class AssignLoss(torch.autograd.Function):
+        """Mean matched squared distance of point-cloud pairs.
+
+        forward: the batched solver (costs |x - y|^2 scaled per pair so the
+        largest is 1, Eq. 1 rounding, Sec. 2.2 phases) gives a plan sigma per
+        pair; the loss is (1/n) sum_i |x_i - y_sigma(i)|^2 in input units.
+        backward: the hand-written CUDA kernel with the plans held fixed.
+        """
+
+        @staticmethod
+        def forward(ctx, X, Y, eps):
+            B, n, d = X.shape
+            sizes = [n] * B
+            res = assign_batched_points(Y.detach().reshape(B * n, d), X.detach().reshape(B * n, d),
+                                        sizes, eps, metric="sqeuclidean", sync=False)
+            ctx.save_for_backward(X, Y, res["row_to_col"])
+            ctx.plan = res
+            return (res["costs"] / n).to(X.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            X, Y, r2c = ctx.saved_tensors
+            gX, gY = assign_backward(r2c, X.detach(), Y.detach(), g)
+            return gX, gY, None
+
+    return AssignLoss
+
+
+_AssignLoss = None
+
+
+def __getattr__(name):
+    global _AssignLoss
+    if name == "AssignLoss":
+        if _AssignLoss is None:
+            _AssignLoss = _assign_loss_function()
+        return _AssignLoss
+    raise AttributeError(name)
+
+
+def assignment_loss(X, Y, eps: float):
+    """Differentiable (batch,) loss for (batch, n, dim) FP32 CUDA point clouds."""
+    return __getattr__("AssignLoss").apply(X, Y, eps)

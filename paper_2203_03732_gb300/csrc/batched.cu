@@ -308,7 +308,9 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_bsolve(BParams p) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ BShared s;
-    const int nmax = p.n_max;
+    // region sizes use n_max rounded up to a multiple of 8, so every region
+    // (8-byte words, int2 pairs, the uint4-read key copy) starts 16-byte aligned
+    const int nmax = (p.n_max + 7) & ~7;
     unsigned long long *pw = reinterpret_cast<unsigned long long *>(dyn);
     int *yb = reinterpret_cast<int *>(pw + nmax);
     int *fl0 = yb + nmax;
@@ -519,8 +521,10 @@ __global__ void __launch_bounds__(THREADS) k_bsolve(BParams p) {
 
 size_t bsolve_smem(int n_max, int ldq_max, int threads) {
     // pw (8) + yb (4) + fl 2x(4) + ql 2x(8) + won (4) per row, keys 2 per column;
-    // the cost reduction reuses the front as one double per thread
-    const size_t state = (size_t)n_max * (8 + 4 + 8 + 16 + 4) + (size_t)ldq_max * 2;
+    // rows padded to a multiple of 8 as in k_bsolve; the cost reduction reuses
+    // the front as one double per thread
+    const size_t rows = (size_t)((n_max + 7) & ~7);
+    const size_t state = rows * (8 + 4 + 8 + 16 + 4) + (size_t)ldq_max * 2;
     const size_t red = (size_t)threads * sizeof(double);
     return state > red ? state : red;
 }
