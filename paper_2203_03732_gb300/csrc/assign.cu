@@ -53,7 +53,8 @@ constexpr int kMaxGrid = 1023;            // barrier payload field width
 // Control block at the start of the workspace.
 struct Ctl {
     WsHead head;
-    unsigned long long bar_slot[4];  // barrier h accumulates arrivals + payload in slot h % 4
+    unsigned long long bar_slot[4][2];  // barrier h: arrivals + payload, pool donations
+    int pool_cnt[2];                    // pool fill counters, by phase parity
     int free_at_stop;
     int pad0;
     long long phases;
@@ -68,14 +69,14 @@ struct Ctl {
 };
 
 struct Layout {
-    size_t ctl, cb, ka, prop, won, lists, total;
+    size_t ctl, cb, ka, prop, won, pool, lists, total;
     int ldq, won_words;
     size_t list_stride;  // ints per CTA in the list region
 };
 
-// Per-CTA overflow storage: two row lists (this phase, next phase) and two
-// proposal lists of (b, a) pairs (this round, previous round), each able to
-// hold every row.
+// Per-CTA overflow storage: two proposal lists of (b, a) pairs (this round,
+// previous round), each able to hold every row; the shared pool of free rows
+// (two buffers by phase parity).
 Layout make_layout(int nB, int nA, int grid) {
     Layout L;
     Carver c;
@@ -86,7 +87,8 @@ Layout make_layout(int nB, int nA, int grid) {
     L.prop = c.take<unsigned long long>((size_t)nA);
     L.won_words = (nA + 31) / 32;
     L.won = c.take<unsigned>(3 * (size_t)L.won_words);
-    L.list_stride = 6 * (size_t)nB;
+    L.pool = c.take<int>(2 * (size_t)nB);
+    L.list_stride = 4 * (size_t)nB;
     L.lists = c.take<int>((size_t)grid * L.list_stride);
     L.total = c.total();
     return L;
@@ -100,6 +102,7 @@ struct Params {
     unsigned long long *prop;
     unsigned *won;  // [3][won_words] first proposals of rounds R % 3
     int won_words;
+    int *pool;  // [2][nB]
     int *lists;
     size_t list_stride;
     int nB, nA, ldq, T;
@@ -218,33 +221,27 @@ __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
 // CTA's private region of the workspace.
 // ---------------------------------------------------------------------------
 struct Smem {
-    int fl[2][kListSm];       // rows of this phase / next phase
+    int fl[2][kListSm];       // kept rows of this phase / next phase
     int2 ql[2][kListSm];      // (b, a) proposals of this round / previous round
     int job_b[kBatch];
     int job_start[kBatch];
+    int job_tgt[kBatch];
+    int job_best[kBatch];
+    int don[kBatch];          // rows given to the pool in this batch
     int best[kWarps];
     int nfl[2], nql[2];
-    int njob;
-    int had_prop, nonfirst, nf_delta;
+    int njob, ndon, don_base;
+    int had_prop, nonfirst, nf_delta, donated;
     unsigned long long bytes;
     unsigned long long rows;
-    unsigned long long pub;
+    unsigned long long pub, pub2;
     int err;
 };
 
 struct Lists {
-    int *fl[2];   // global overflow of fl
     int2 *ql[2];  // global overflow of ql
 };
 
-__device__ __forceinline__ void fl_push(Smem &s, const Lists &g, int which, int v) {
-    const int i = atomicAdd(&s.nfl[which], 1);
-    if (i < kListSm) s.fl[which][i] = v;
-    else g.fl[which][i - kListSm] = v;
-}
-__device__ __forceinline__ int fl_get(const Smem &s, const Lists &g, int which, int i) {
-    return i < kListSm ? s.fl[which][i] : g.fl[which][i - kListSm];
-}
 __device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a) {
     const int i = atomicAdd(&s.nql[which], 1);
     if (i < kListSm) s.ql[which][i] = make_int2(b, a);
@@ -254,21 +251,36 @@ __device__ __forceinline__ int2 ql_get(const Smem &s, const Lists &g, int which,
     return i < kListSm ? s.ql[which][i] : g.ql[which][i - kListSm];
 }
 
+// A row of the next phase's B': the CTA keeps up to `keep` of them, the rest
+// go to the pool that every CTA draws from at the next phase start.
+__device__ __forceinline__ void push_next(Smem &s, int nxt, int keep, int v) {
+    const int i = atomicAdd(&s.nfl[nxt], 1);
+    if (i < keep) s.fl[nxt][i] = v;
+    else s.don[atomicAdd(&s.ndon, 1)] = v;
+    atomicAdd(&s.nf_delta, 1);
+}
+
 // Grid barrier carrying a payload.  Barrier h adds, for each CTA,
 //   1 (arrival) | had_prop << 10 | nonfirst << 20 | nf_delta << 40
-// (had_prop, nonfirst in {0,1}; nf_delta < 2^24; at most 1023 CTAs) to slot
-// h % 4 with one release reduction, then spins (bounded) with acquire loads
-// until the slot's arrival field reaches the grid size; the slot then holds
-// the totals.  CTA 0 zeroes slot (h + 2) % 4 during round h: every CTA read
-// it before arriving at barrier h - 1, and it is reused by barrier h + 2.
+// (had_prop, nonfirst in {0,1}; nf_delta < 2^24; at most 1023 CTAs) to word 0
+// of slot h % 4 with a release reduction, after adding its pool donations to
+// word 1; it then spins (bounded) with acquire loads until the arrival field
+// reaches the grid size.  CTA 0 zeroes slot (h + 2) % 4 during round h: every
+// CTA read it before arriving at barrier h - 1, and barrier h + 2 reuses it.
 // Returns false when the kernel must stop.
 __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsigned G,
-                                          long long limit, unsigned long long mine) {
+                                          long long limit, unsigned long long mine,
+                                          unsigned long long donated) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned h = gen + 1;
-        unsigned long long *slot = &ctl->bar_slot[h & 3];
-        if (blockIdx.x == 0) ctl->bar_slot[(h + 2) & 3] = 0;
+        unsigned long long *slot = ctl->bar_slot[h & 3];
+        if (blockIdx.x == 0) {
+            ctl->bar_slot[(h + 2) & 3][0] = 0;
+            ctl->bar_slot[(h + 2) & 3][1] = 0;
+        }
+        if (donated)
+            asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(slot + 1), "l"(donated) : "memory");
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(slot), "l"(mine) : "memory");
         unsigned long long v = 0;
         const long long t0 = clock64();
@@ -288,6 +300,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
         }
         const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
         s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
+        s.pub2 = ok ? ld_relaxed_u64(slot + 1) : 0;
         s.err = ok ? 0 : 1;
     }
     __syncthreads();
@@ -295,14 +308,18 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
     return s.err == 0;
 }
 
-// Scan queued jobs rows_per_group rows at a time with warps_per_row warps per
-// row, then propose (atomicMax) or relabel.
+// The queued jobs: one parallel read of every job's y(b); then the row scans,
+// rows_per_group rows at a time with warps_per_row warps per row; then every
+// proposal (atomicMax) or relabel at once; then the pool donations.
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const uint16_t *ks, const unsigned *tk, unsigned *won_now,
-                                         unsigned R, unsigned Rps, int cur, int qcur,
-                                         int warps_per_row, int rows_per_group) {
+                                         unsigned R, unsigned Rps, int nxt, int qcur, int keep,
+                                         int *pool_next, int *pool_cnt, int warps_per_row,
+                                         int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
+    for (int j = threadIdx.x; j < nq; j += blockDim.x)
+        s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
         const int ng = min(rows_per_group, nq - g0);
         if (threadIdx.x < ng) s.best[threadIdx.x] = 0x7FFFFFFF;
@@ -313,7 +330,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
             const int b = s.job_b[g0 + slot];
             const int start = s.job_start[g0 + slot];
             const int s8 = start & ~7;
-            const uint32_t tgt = (uint32_t)(ld_relaxed_s32(p.y_b + b) - 1);
+            const uint32_t tgt = (uint32_t)s.job_tgt[g0 + slot];
             const uint16_t *row = p.cb + (size_t)b * p.ldq;
             volatile int *vbest = &s.best[slot];
             for (int c0 = s8 + sub * kChunk; c0 < p.ldq; c0 += warps_per_row * kChunk) {
@@ -329,39 +346,47 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         }
         if (lane == 0 && my_bytes) atomicAdd(&s.bytes, my_bytes);
         __syncthreads();
-        if (threadIdx.x < ng) {
-            const int b = s.job_b[g0 + threadIdx.x];
-            const int a = s.best[threadIdx.x];
-            if (a != 0x7FFFFFFF) {
-                const unsigned long long old = atomicMax(p.prop + a, word_of(R, b));
-                const unsigned t = tag_of(old);
-                if (t < Rps) {
-                    // first proposal to a in this phase: a is won this round
-                    // (step III a: y(a) -= eps, applied to the key copies at
-                    // the next phase) and its old partner is evicted (step II)
-                    // into the next phase's B'.
-                    atomicOr(won_now + (a >> 5), 1u << (a & 31));
-                    // +1 on the 16-bit output key at L2 (no carry leaves the half: k <= 32768)
-                    atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
-                    const int partner = row_of(old);
-                    if (partner >= 0) {
-                        fl_push(s, g, cur ^ 1, partner);
-                        atomicAdd(&s.nf_delta, 1);
-                    }
-                } else if (t == R) {
-                    s.nonfirst = 1;
-                } else {
-                    record_error(&p.ctl->head, PR_ERR_INTERNAL);
-                }
-                ql_push(s, g, qcur, b, a);
-                s.had_prop = 1;
+        if (threadIdx.x < ng) s.job_best[g0 + threadIdx.x] = s.best[threadIdx.x];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        const int b = s.job_b[j];
+        const int a = s.job_best[j];
+        if (a != 0x7FFFFFFF) {
+            const unsigned long long old = atomicMax(p.prop + a, word_of(R, b));
+            const unsigned t = tag_of(old);
+            if (t < Rps) {
+                // first proposal to a in this phase: a is won this round
+                // (step III a: y(a) -= eps, applied to the key copies at the
+                // next phase) and its old partner is evicted (step II) into
+                // the next phase's B'.
+                atomicOr(won_now + (a >> 5), 1u << (a & 31));
+                // +1 on the 16-bit output key at L2 (no carry leaves the half: k <= 32768)
+                atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
+                const int partner = row_of(old);
+                if (partner >= 0) push_next(s, nxt, keep, partner);
+            } else if (t == R) {
+                s.nonfirst = 1;
             } else {
-                atomicAdd(p.y_b + b, 1);  // step (III b): free w.r.t. M' -> relabel
-                fl_push(s, g, cur ^ 1, b);
-                atomicAdd(&s.nf_delta, 1);
+                record_error(&p.ctl->head, PR_ERR_INTERNAL);
             }
+            ql_push(s, g, qcur, b, a);
+            s.had_prop = 1;
+        } else {
+            atomicAdd(p.y_b + b, 1);  // step (III b): free w.r.t. M' -> relabel
+            push_next(s, nxt, keep, b);
         }
+    }
+    __syncthreads();
+    if (s.ndon > 0) {
+        if (threadIdx.x == 0) s.don_base = atomicAdd(pool_cnt, s.ndon);
         __syncthreads();
+        for (int i = threadIdx.x; i < s.ndon; i += blockDim.x) pool_next[s.don_base + i] = s.don[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s.donated += s.ndon;
+            s.ndon = 0;
+        }
     }
     if (threadIdx.x == 0) {
         s.rows += (unsigned long long)nq;
@@ -373,14 +398,14 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
 // ---------------------------------------------------------------------------
 // k_phases: every phase of Sec. 2.2 in one cooperative launch.
 //
-// Each CTA owns a set of free rows.  Phase 0 deals rows b = cta + k*G.  A row
-// that relabels stays with its CTA for the next phase; a row evicted by a
-// first proposal joins that proposer's CTA.  Round R of a phase scans the
-// CTA's jobs (all its rows in the first round; afterwards the rows whose
-// proposal lost, resuming after the lost column), then one payload barrier.
-// If no column received two proposals in round R every proposal won and the
-// phase is over; otherwise each CTA rereads its proposals' words to find the
-// losers and runs round R + 1.
+// Phase 0 deals rows b = cta + k*G.  Afterwards each CTA keeps up to `keep`
+// of the rows it relabelled or evicted; the others go to a pool, dealt out
+// cyclically at the next phase start.  Round R of a phase scans the CTA's
+// jobs (its rows in the first round; afterwards the rows whose proposal lost,
+// resuming after the lost column), then one payload barrier.  If no column
+// received two proposals in round R every proposal won and the phase is over;
+// otherwise each CTA rereads its proposals' words to find the losers and runs
+// round R + 1.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
@@ -391,19 +416,18 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
+    const int keep = rows_per_group > 1 ? rows_per_group - 1 : 1;
     Lists g;
     int *base = p.lists + (size_t)cta * p.list_stride;
-    g.fl[0] = base;
-    g.fl[1] = base + p.nB;
-    g.ql[0] = reinterpret_cast<int2 *>(base + 2 * (size_t)p.nB);
-    g.ql[1] = reinterpret_cast<int2 *>(base + 4 * (size_t)p.nB);
+    g.ql[0] = reinterpret_cast<int2 *>(base);
+    g.ql[1] = reinterpret_cast<int2 *>(base + 2 * (size_t)p.nB);
 
     for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
         reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
     for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) tk[i] = 0;
     if (threadIdx.x == 0) {
         s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
-        s.njob = 0;
+        s.njob = s.ndon = 0;
         s.bytes = s.rows = 0;
         s.err = 0;
     }
@@ -413,11 +437,18 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     unsigned R = 0;  // global round counter (round tags)
     long long phase = 0, rounds = 0;
     int cur = 0, qcur = 0;
+    long long pool_size = 0;  // rows in this phase's pool
     const int first_items = cta < p.nB ? (p.nB - 1 - cta) / (int)G + 1 : 0;
     for (;;) {
         // ---- one phase ----
         const unsigned Rps = R + 1;
-        long long nf_next = 0;
+        const int pq = (int)(phase & 1);
+        const int *pool_now = p.pool + (size_t)pq * p.nB;
+        int *pool_next = p.pool + (size_t)(pq ^ 1) * p.nB;
+        if (cta == 0 && threadIdx.x == 0) ctl->pool_cnt[pq] = 0;  // for phase + 1's donations
+        const int kept = phase == 0 ? first_items : min(s.nfl[cur], keep);
+        const int from_pool = (pool_size > cta) ? (int)((pool_size - 1 - cta) / (long long)G) + 1 : 0;
+        long long nf_next = 0, pool_next_size = 0;
         bool first_round = true;
         for (;;) {
             ++R;
@@ -449,20 +480,24 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 s.had_prop = 0;
                 s.nonfirst = 0;
                 s.nf_delta = 0;
+                s.donated = 0;
                 s.nql[qcur] = 0;
             }
             __syncthreads();
             const unsigned long long t_r1 = p.profile ? gtimer() : 0;
-            // items of this round: the phase's rows, or last round's proposals
-            const int nitems = first_round ? (phase == 0 ? first_items : s.nfl[cur]) : s.nql[qcur ^ 1];
+            // items of this round: kept rows + pool share, or last round's proposals
+            const int nitems = first_round ? kept + from_pool : s.nql[qcur ^ 1];
             for (int i0 = 0; i0 < nitems; i0 += kBatch) {
                 const int cnt = min(kBatch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                    const int it = i0 + i;
                     int b, start = 0;
                     if (first_round) {
-                        b = phase == 0 ? cta + (i0 + i) * (int)G : fl_get(s, g, cur, i0 + i);
+                        if (phase == 0) b = cta + it * (int)G;
+                        else if (it < kept) b = s.fl[cur][it];
+                        else b = ld_relaxed_s32(pool_now + cta + (long long)(it - kept) * G);
                     } else {
-                        const int2 q = ql_get(s, g, qcur ^ 1, i0 + i);
+                        const int2 q = ql_get(s, g, qcur ^ 1, it);
                         b = q.x;
                         const unsigned long long w = ld_relaxed_u64(p.prop + q.y);
                         if (row_of(w) == b) continue;  // won: matched, leaves B'
@@ -473,7 +508,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     s.job_start[j] = start;
                 }
                 __syncthreads();
-                run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur, qcur, warps_per_row, rows_per_group);
+                run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
+                         &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group);
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
                                             ((unsigned long long)s.nonfirst << 20) |
@@ -488,7 +524,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     ctl->prof_slot[(R + 1) & 1][1] = 0;
                 }
             }
-            if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine)) goto done;
+            if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)) goto done;
             if (p.profile && cta == 0 && threadIdx.x == 0) {
                 const unsigned long long t_r3 = gtimer();
                 ctl->prof[0] += t_r1 - t_r0;
@@ -501,6 +537,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             const unsigned long long pub = s.pub;
             if ((pub >> 31) & 1ull) ++rounds;
             nf_next += (long long)(pub & 0x3FFFFFFFull);
+            pool_next_size += (long long)s.pub2;
             first_round = false;
             qcur ^= 1;
             if (!((pub >> 30) & 1ull)) break;  // no contested column: phase over
@@ -508,6 +545,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         ++phase;
         if (threadIdx.x == 0) s.nfl[cur] = 0;
         cur ^= 1;
+        pool_size = pool_next_size;
         if (nf_next <= p.T) {
             if (cta == 0 && threadIdx.x == 0) ctl->free_at_stop = (int)nf_next;
             break;
@@ -700,6 +738,7 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.prop = (unsigned long long *)(w + L.prop);
     p.won = (unsigned *)(w + L.won);
     p.won_words = L.won_words;
+    p.pool = (int *)(w + L.pool);
     p.lists = (int *)(w + L.lists);
     p.list_stride = L.list_stride;
     p.nB = n_rows;
