@@ -46,7 +46,8 @@ constexpr int kThreads = 512;             // threads per CTA of the phase kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kUnroll = 8;                // 16-byte loads in flight per lane per chunk
 constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk (4 KiB)
-constexpr int kListSm = 2048;             // list entries kept in shared memory
+constexpr int kListSm = 1024;             // proposal-list entries kept in shared memory
+constexpr int kKeepMax = 16;              // rows a CTA may keep for its next phase
 constexpr int kBatch = 256;               // items turned into scan jobs at a time
 constexpr int kMaxGrid = 1023;            // barrier payload field width
 
@@ -87,8 +88,8 @@ Layout make_layout(int nB, int nA, int grid) {
     L.prop = c.take<unsigned long long>((size_t)nA);
     L.won_words = (nA + 31) / 32;
     L.won = c.take<unsigned>(3 * (size_t)L.won_words);
-    L.pool = c.take<int>(2 * (size_t)nB);
-    L.list_stride = 4 * (size_t)nB;
+    L.pool = c.take<int2>(2 * (size_t)nB);
+    L.list_stride = 8 * (size_t)nB;
     L.lists = c.take<int>((size_t)grid * L.list_stride);
     L.total = c.total();
     return L;
@@ -102,7 +103,7 @@ struct Params {
     unsigned long long *prop;
     unsigned *won;  // [3][won_words] first proposals of rounds R % 3
     int won_words;
-    int *pool;  // [2][nB]
+    int2 *pool;  // [2][nB] (b, y(b) or -1)
     int *lists;
     size_t list_stride;
     int nB, nA, ldq, T;
@@ -221,13 +222,13 @@ __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
 // CTA's private region of the workspace.
 // ---------------------------------------------------------------------------
 struct Smem {
-    int fl[2][kListSm];       // kept rows of this phase / next phase
-    int2 ql[2][kListSm];      // (b, a) proposals of this round / previous round
+    int2 fl[2][kKeepMax];     // kept (b, y(b) or -1) of this phase / next phase
+    int4 ql[2][kListSm];      // (b, a, y(b)) proposals of this round / previous round
     int job_b[kBatch];
     int job_start[kBatch];
     int job_tgt[kBatch];
     int job_best[kBatch];
-    int don[kBatch];          // rows given to the pool in this batch
+    int2 don[kBatch];         // (b, y(b) or -1) given to the pool in this batch
     int best[kWarps];
     int nfl[2], nql[2];
     int njob, ndon, don_base;
@@ -239,24 +240,24 @@ struct Smem {
 };
 
 struct Lists {
-    int2 *ql[2];  // global overflow of ql
+    int4 *ql[2];  // global overflow of ql
 };
 
-__device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a) {
+__device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a, int y) {
     const int i = atomicAdd(&s.nql[which], 1);
-    if (i < kListSm) s.ql[which][i] = make_int2(b, a);
-    else g.ql[which][i - kListSm] = make_int2(b, a);
+    if (i < kListSm) s.ql[which][i] = make_int4(b, a, y, 0);
+    else g.ql[which][i - kListSm] = make_int4(b, a, y, 0);
 }
-__device__ __forceinline__ int2 ql_get(const Smem &s, const Lists &g, int which, int i) {
+__device__ __forceinline__ int4 ql_get(const Smem &s, const Lists &g, int which, int i) {
     return i < kListSm ? s.ql[which][i] : g.ql[which][i - kListSm];
 }
 
 // A row of the next phase's B': the CTA keeps up to `keep` of them, the rest
 // go to the pool that every CTA draws from at the next phase start.
-__device__ __forceinline__ void push_next(Smem &s, int nxt, int keep, int v) {
+__device__ __forceinline__ void push_next(Smem &s, int nxt, int keep, int b, int y) {
     const int i = atomicAdd(&s.nfl[nxt], 1);
-    if (i < keep) s.fl[nxt][i] = v;
-    else s.don[atomicAdd(&s.ndon, 1)] = v;
+    if (i < keep) s.fl[nxt][i] = make_int2(b, y);
+    else s.don[atomicAdd(&s.ndon, 1)] = make_int2(b, y);
     atomicAdd(&s.nf_delta, 1);
 }
 
@@ -314,12 +315,12 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const uint16_t *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
-                                         int *pool_next, int *pool_cnt, int warps_per_row,
+                                         int2 *pool_next, int *pool_cnt, int warps_per_row,
                                          int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
     for (int j = threadIdx.x; j < nq; j += blockDim.x)
-        s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
+        if (s.job_tgt[j] < 0) s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
         const int ng = min(rows_per_group, nq - g0);
         if (threadIdx.x < ng) s.best[threadIdx.x] = 0x7FFFFFFF;
@@ -364,17 +365,17 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 // +1 on the 16-bit output key at L2 (no carry leaves the half: k <= 32768)
                 atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
                 const int partner = row_of(old);
-                if (partner >= 0) push_next(s, nxt, keep, partner);
+                if (partner >= 0) push_next(s, nxt, keep, partner, -1);
             } else if (t == R) {
                 s.nonfirst = 1;
             } else {
                 record_error(&p.ctl->head, PR_ERR_INTERNAL);
             }
-            ql_push(s, g, qcur, b, a);
+            ql_push(s, g, qcur, b, a, s.job_tgt[j] + 1);
             s.had_prop = 1;
         } else {
             atomicAdd(p.y_b + b, 1);  // step (III b): free w.r.t. M' -> relabel
-            push_next(s, nxt, keep, b);
+            push_next(s, nxt, keep, b, s.job_tgt[j] + 2);
         }
     }
     __syncthreads();
@@ -416,11 +417,11 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
-    const int keep = rows_per_group > 1 ? rows_per_group - 1 : 1;
+    const int keep = rows_per_group > 1 ? min(rows_per_group - 1, kKeepMax) : 1;
     Lists g;
     int *base = p.lists + (size_t)cta * p.list_stride;
-    g.ql[0] = reinterpret_cast<int2 *>(base);
-    g.ql[1] = reinterpret_cast<int2 *>(base + 2 * (size_t)p.nB);
+    g.ql[0] = reinterpret_cast<int4 *>(base);
+    g.ql[1] = reinterpret_cast<int4 *>(base + 4 * (size_t)p.nB);
 
     for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
         reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
@@ -443,8 +444,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         // ---- one phase ----
         const unsigned Rps = R + 1;
         const int pq = (int)(phase & 1);
-        const int *pool_now = p.pool + (size_t)pq * p.nB;
-        int *pool_next = p.pool + (size_t)(pq ^ 1) * p.nB;
+        const int2 *pool_now = p.pool + (size_t)pq * p.nB;
+        int2 *pool_next = p.pool + (size_t)(pq ^ 1) * p.nB;
         if (cta == 0 && threadIdx.x == 0) ctl->pool_cnt[pq] = 0;  // for phase + 1's donations
         const int kept = phase == 0 ? first_items : min(s.nfl[cur], keep);
         const int from_pool = (pool_size > cta) ? (int)((pool_size - 1 - cta) / (long long)G) + 1 : 0;
@@ -454,12 +455,38 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             ++R;
             const unsigned long long t_r0 = p.profile ? gtimer() : 0;
             unsigned *won_now = p.won + (size_t)(R % 3) * p.won_words;
+            if (threadIdx.x == 0) {
+                s.had_prop = 0;
+                s.nonfirst = 0;
+                s.nf_delta = 0;
+                s.donated = 0;
+                s.nql[qcur] = 0;
+            }
+            // items of this round: kept rows + pool share, or last round's proposals
+            const int nitems = first_round ? kept + from_pool : s.nql[qcur ^ 1];
+            // Issue this thread's first item load and its bitmap-word load
+            // before using either, so the two global reads overlap.
+            int2 pre_pool = make_int2(0, 0);
+            unsigned long long pre_word = 0;
+            int4 pre_q = make_int4(0, 0, 0, 0);
+            const int it0 = threadIdx.x;
+            if (it0 < nitems && it0 < kBatch) {
+                if (first_round) {
+                    if (phase > 0 && it0 >= kept)
+                        pre_pool = ld_relaxed_int2(pool_now + cta + (long long)(it0 - kept) * G);
+                } else {
+                    pre_q = ql_get(s, g, qcur ^ 1, it0);
+                    pre_word = ld_relaxed_u64(p.prop + pre_q.y);
+                }
+            }
+            const unsigned *wprev = p.won + (size_t)((R + 2) % 3) * p.won_words;
+            unsigned pre_m = 0;
+            if (R > 1 && threadIdx.x < p.won_words) pre_m = ld_relaxed_u32(wprev + threadIdx.x);
             if (R > 1) {
                 // first proposals of round R - 1 join the taken set; a new
                 // phase first moves the finished phase's set into the keys
-                const unsigned *wprev = p.won + (size_t)((R + 2) % 3) * p.won_words;
                 for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) {
-                    unsigned m = ld_relaxed_u32(wprev + i);
+                    unsigned m = i == (int)threadIdx.x ? pre_m : ld_relaxed_u32(wprev + i);
                     if (first_round) {
                         m |= tk[i];
                         tk[i] = 0;
@@ -476,36 +503,39 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 for (int i = cta * blockDim.x + threadIdx.x; i < p.won_words; i += G * blockDim.x)
                     wold[i] = 0;
             }
-            if (threadIdx.x == 0) {
-                s.had_prop = 0;
-                s.nonfirst = 0;
-                s.nf_delta = 0;
-                s.donated = 0;
-                s.nql[qcur] = 0;
-            }
             __syncthreads();
             const unsigned long long t_r1 = p.profile ? gtimer() : 0;
-            // items of this round: kept rows + pool share, or last round's proposals
-            const int nitems = first_round ? kept + from_pool : s.nql[qcur ^ 1];
             for (int i0 = 0; i0 < nitems; i0 += kBatch) {
                 const int cnt = min(kBatch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                     const int it = i0 + i;
-                    int b, start = 0;
+                    const bool pre = i0 == 0 && i == (int)threadIdx.x;  // loaded above
+                    int b, y = -1, start = 0;
                     if (first_round) {
-                        if (phase == 0) b = cta + it * (int)G;
-                        else if (it < kept) b = s.fl[cur][it];
-                        else b = ld_relaxed_s32(pool_now + cta + (long long)(it - kept) * G);
+                        if (phase == 0) {
+                            b = cta + it * (int)G;
+                            y = 1;
+                        } else if (it < kept) {
+                            const int2 e = s.fl[cur][it];
+                            b = e.x;
+                            y = e.y;
+                        } else {
+                            const int2 e = pre ? pre_pool : ld_relaxed_int2(pool_now + cta + (long long)(it - kept) * G);
+                            b = e.x;
+                            y = e.y;
+                        }
                     } else {
-                        const int2 q = ql_get(s, g, qcur ^ 1, it);
+                        const int4 q = pre ? pre_q : ql_get(s, g, qcur ^ 1, it);
+                        const unsigned long long w = pre ? pre_word : ld_relaxed_u64(p.prop + q.y);
                         b = q.x;
-                        const unsigned long long w = ld_relaxed_u64(p.prop + q.y);
                         if (row_of(w) == b) continue;  // won: matched, leaves B'
                         start = q.y + 1;               // lost: resume after a
+                        y = q.z;
                     }
                     const int j = atomicAdd(&s.njob, 1);
                     s.job_b[j] = b;
                     s.job_start[j] = start;
+                    s.job_tgt[j] = y >= 0 ? y - 1 : -1;
                 }
                 __syncthreads();
                 run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
@@ -738,7 +768,7 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.prop = (unsigned long long *)(w + L.prop);
     p.won = (unsigned *)(w + L.won);
     p.won_words = L.won_words;
-    p.pool = (int *)(w + L.pool);
+    p.pool = (int2 *)(w + L.pool);
     p.lists = (int *)(w + L.lists);
     p.list_stride = L.list_stride;
     p.nB = n_rows;
