@@ -106,8 +106,8 @@ def _declare(L):
     L.or_cost_f32.restype = c_dbl
     L.or_hungarian.argtypes = [_f64p, c_i64, c_i32, c_i32, _i32p]
     L.or_hungarian.restype = c_dbl
-    if hasattr(L, "or_ot_cluster"):
-        from . import ot as _ot  # noqa: F401  (declares its own symbols)
+    if hasattr(L, "or_ot_cluster_int"):
+        from . import ot as _ot
         _ot._declare(L)
     if hasattr(L, "or_assign_points"):
         from . import points as _pts
@@ -119,7 +119,7 @@ def _declare(L):
 # --------------------------------------------------------------------------
 
 def quantise(C: np.ndarray, eps: float) -> np.ndarray:
-    """Eq. (1) in eps units: cb = floor(C / eps) (FP64 divide), int32."""
+    """Eq. (1) in eps units: cb = floor of the exact quotient C / eps, int32."""
     C = np.ascontiguousarray(C)
     nB, nA = C.shape
     cb = np.empty((nB, nA), dtype=np.int32)

@@ -48,4 +48,28 @@ int or_assign_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA, double ep
                   or_stats *st);
 double or_hungarian(const double *C, int64_t ldc, int32_t nB, int32_t nA, int32_t *row_to_col);
 
+/* optimal transport (Sec. 4), cluster form */
+int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *S, const int32_t *D,
+                      int64_t T, int32_t mode, int64_t phase_cap, int32_t *F, int32_t *f,
+                      int32_t *kmin, int32_t *clo, int32_t *chi, int32_t *plan_lo,
+                      int32_t *plan_hi, or_stats *st);
+int64_t or_ot_check(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *F, const int32_t *f,
+                    const int32_t *kmin, const int32_t *clo, const int32_t *chi, const void *unused);
+double or_ot_theta(int32_t nB, int32_t nA, double eps);
+int or_ot_counts(const double *nu, const double *mu, int32_t nB, int32_t nA, double eps,
+                 int32_t *S, int32_t *D);
+double or_ot_fixup(const double *C, int64_t ldc, int32_t nB, int32_t nA, const double *nu,
+                   const double *mu, double theta, const int32_t *plan_cnt, double *mass);
+
+/* points forms */
+void or_points_cost(const float *XA, const float *XB, int32_t nA, int32_t nB, int32_t dim,
+                    int32_t squared, float *C);
+double or_points_match_cost(const float *XA, const float *XB, int32_t nB, int32_t dim,
+                            int32_t squared, const int32_t *row_to_col);
+int or_assign_points(const float *XA, const float *XB, int32_t nA, int32_t nB, int32_t dim,
+                     int32_t squared, double eps, int32_t *match_b, int32_t *match_a,
+                     int32_t *y_b, int32_t *y_a, double *cost, or_stats *st);
+void or_sqeuclid_backward(const float *X, const float *Y, int32_t n, int32_t dim,
+                          const int32_t *row_to_col, float g, float *gX, float *gY);
+
 #endif

@@ -1,0 +1,127 @@
+"""Pins for the OT oracle (Sec. 4), CPU only: one copy per vertex reduces to
+the assignment routine; invariants and the two-cluster lemma on the implied
+copy state; plan feasibility; the additive bound against an exact LP (scipy
+HiGHS); hand-computed mass quantisation."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ot as O
+from paper_2203_03732_gb300 import workloads as W
+
+
+def lp_opt(C, nu, mu):
+    from scipy.optimize import linprog
+    nB, nA = C.shape
+    A_eq = np.zeros((nB, nB * nA))
+    for b in range(nB):
+        A_eq[b, b * nA:(b + 1) * nA] = 1
+    A_ub = np.zeros((nA, nB * nA))
+    for a in range(nA):
+        A_ub[a, a::nA] = 1
+    r = linprog(C.ravel(), A_ub=A_ub, b_ub=mu, A_eq=A_eq, b_eq=nu, bounds=(0, None), method="highs")
+    assert r.status == 0
+    return r.fun
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("eps", [0.1, 0.02])
+def test_unit_copies_equal_assignment(seed, eps):
+    """With one copy per vertex the cluster phases are the Sec. 2.2 routine."""
+    n = 60
+    C = W.assignment_euclid_2d(n, seed)
+    cb = oracle.quantise(C, eps)
+    T = oracle.threshold(eps, n)
+    a = oracle.assign_int(cb, T)
+    r = O.cluster_int(cb, np.ones(n, np.int32), np.ones(n, np.int32), T)
+    assert r["stats"]["phases"] == a["stats"]["phases"]
+    assert r["stats"]["rounds"] == a["stats"]["rounds"]
+    assert r["stats"]["free_at_stop"] == a["stats"]["free_at_stop"]
+    plan = r["plan_lo"] + r["plan_hi"]
+    mb = np.where(plan.sum(1) > 0, plan.argmax(1), -1)
+    assert np.array_equal(mb, a["match_b"])
+    assert np.array_equal(r["F"], a["y_b"])
+    assert np.array_equal(-r["kmin"], a["y_a"])
+
+
+def copy_state_check(r, cb):
+    """(I1)/(I2) and Lemma 4.1 on the copy instance the cluster state stands
+    for: free supply copies of b have dual F_b; a matched copy in plan_lo /
+    plan_hi at (b, a) has dual cbar + kmin_a / cbar + kmin_a + 1; a's copies
+    have keys kmin_a (clo of them) and kmin_a + 1 (chi)."""
+    F, f, kmin, clo, chi = r["F"], r["f"], r["kmin"], r["clo"], r["chi"]
+    plo, phi = r["plan_lo"], r["plan_hi"]
+    nB, nA = cb.shape
+    assert (r["S"] == f + plo.sum(1) + phi.sum(1)).all()
+    assert (phi.sum(0) == chi).all()
+    assert ((kmin == 0) | (plo.sum(0) == clo)).all()
+    assert ((kmin >= 1) | (plo.sum(0) == 0)).all()
+    for b in range(nB):
+        duals = set()
+        if f[b] > 0:
+            duals.add(int(F[b]))
+        for a in range(nA):
+            if plo[b, a]:
+                duals.add(int(cb[b, a] + kmin[a]))
+            if phi[b, a]:
+                duals.add(int(cb[b, a] + kmin[a] + 1))
+        if not duals:
+            continue
+        assert max(duals) <= F[b]               # raise rule: F_b is the largest
+        if plo[b].sum() + phi[b].sum() > 0:
+            assert max(duals) - min(duals) <= 1  # Lemma 4.1: two clusters
+        # Eq. (2) for every copy of b against a's lowest key (its worst case);
+        # a column without copies constrains nothing
+        has = (clo + chi) > 0
+        for y in duals:
+            assert (y - kmin[has] <= cb[b][has] + 1).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("eps", [0.2, 0.1, 0.05])
+def test_invariants_plan_and_bound(seed, eps):
+    nB, nA = (12, 15) if seed % 2 else (18, 18)
+    C, nu, mu = W.ot_euclid_2d(nB, nA, 100 + seed)
+    r = O.ot(C, nu, mu, eps, mode=oracle.MODE_CHECK)
+    assert r["stats"]["violations"] == 0
+    copy_state_check(r, r["cbar"])
+    assert r["stats"]["free_at_stop"] <= r["T"]
+    m = r["mass"]
+    assert (m >= 0).all()
+    assert np.abs(m.sum(1) - nu).max() <= 1e-12
+    assert (m.sum(0) - mu).max() <= 1e-12
+    opt = lp_opt(C, nu, mu)
+    assert opt - 1e-9 <= r["cost"] <= opt + 3.5 * eps
+
+
+def test_theta_and_counts_by_hand():
+    # n = 3, eps = 0.5: theta = 24; supplies 0.5/0.25/0.25 -> 12/6/6 copies,
+    # demands 1/3 each -> ceil(24/3) = 8 copies.
+    assert O.theta(3, 3, 0.5) == 24.0
+    S, D = O.counts([0.5, 0.25, 0.25], [1 / 3, 1 / 3, 1 / 3], 0.5)
+    assert S.tolist() == [12, 6, 6]
+    assert D.tolist() == [8, 8, 8]
+    # rectangular: n = max(2, 5) = 5, eps = 0.4 -> theta = 50
+    S, D = O.counts([0.7, 0.3], [0.2] * 5, 0.4)
+    assert S.tolist() == [35, 15] and D.tolist() == [10] * 5
+
+
+def test_single_pair():
+    C = np.array([[0.37]])
+    r = O.ot(C, [1.0], [1.0], 0.1)
+    assert r["mass"][0, 0] == 1.0
+    assert abs(r["cost"] - 0.37) < 1e-15
+
+
+def test_zero_masses_and_concentrated_supply():
+    C, nu, mu = W.ot_euclid_2d(8, 10, 7)
+    nu = np.zeros(8)
+    nu[3] = 1.0
+    mu = mu.copy()
+    mu[[0, 4]] = 0.0
+    mu /= mu.sum()
+    r = O.ot(C, nu, mu, 0.1, mode=oracle.MODE_CHECK)
+    assert r["stats"]["violations"] == 0
+    assert np.abs(r["mass"].sum(1) - nu).max() <= 1e-12
+    assert (r["mass"][:, [0, 4]] == 0).all()
+    assert r["cost"] <= lp_opt(C, nu, mu) + 3.5 * 0.1
