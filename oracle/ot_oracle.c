@@ -30,10 +30,10 @@
  *     Proposers resume at the same column next round.  Rounds repeat until
  *     nobody proposes; the result is a maximal matching of the copy graph.
  *   Step II: a grant taking copies of a matched cluster (kmin_a >= 1) evicts
- *     their partners, taken from the most recent matches of a first (a's
- *     kmin-cluster matches form a stack); each evicted copy of b'' rejoins
- *     the free copies of b'' (raised to F_b'').  The granted copies of b are
- *     matched to a at key kmin_a + 1.
+ *     their partners, taken from a's kmin-cluster matches with the highest
+ *     supply index first; each evicted copy of b'' rejoins the free copies of
+ *     b'' (raised to F_b'').  The granted copies of b are matched to a at key
+ *     kmin_a + 1.
  *   Step III: (a) granted copies of a move from kmin_a to kmin_a + 1; when
  *     the kmin cluster is empty the clusters shift up (kmin_a += 1);
  *     (b) every b of B' that kept unplaced free copies has F_b += 1.
@@ -55,24 +55,6 @@
 #include <string.h>
 #include "prot_oracle.h"
 
-typedef struct { int32_t b, cnt; } entry_t;
-typedef struct { entry_t *e; int32_t n, cap; } stack_t_;
-
-static int push_entry(stack_t_ *s, int32_t b, int32_t cnt)
-{
-    if (s->n == s->cap) {
-        int32_t nc = s->cap ? 2 * s->cap : 4;
-        entry_t *ne = (entry_t *)realloc(s->e, sizeof(entry_t) * nc);
-        if (!ne) return -1;
-        s->e = ne;
-        s->cap = nc;
-    }
-    s->e[s->n].b = b;
-    s->e[s->n].cnt = cnt;
-    s->n += 1;
-    return 0;
-}
-
 /* Cluster engine on integer copy counts.  Outputs the final cluster state
  * and the matched copy counts, dense int32 [b * nA + a]: plan_lo counts the
  * copies of b matched to a's cluster at key kmin_a, plan_hi those at key
@@ -84,8 +66,8 @@ int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *
 {
     memset(st, 0, sizeof(*st));
     st->threshold = (int32_t)T;
-    stack_t_ *lo = (stack_t_ *)calloc((size_t)nA, sizeof(stack_t_));
-    stack_t_ *hi = (stack_t_ *)calloc((size_t)nA, sizeof(stack_t_));
+    /* matched copy counts of the two clusters of every a, [a][b] */
+    int32_t *Plo = plan_lo, *Phi = plan_hi;  /* indexed [b * nA + a] as outputs */
     int32_t *r = (int32_t *)malloc(sizeof(int32_t) * nB);
     int32_t *ptr = (int32_t *)malloc(sizeof(int32_t) * nB);
     int32_t *prop = (int32_t *)malloc(sizeof(int32_t) * nB);
@@ -94,10 +76,12 @@ int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *
     int32_t *avail = (int32_t *)malloc(sizeof(int32_t) * nA);
     int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nA);
     int rc = OR_OK;
-    if (!lo || !hi || !r || !ptr || !prop || !searching || !in_bp || !avail || !best) {
+    if (!r || !ptr || !prop || !searching || !in_bp || !avail || !best) {
         rc = OR_ERR_NOMEM;
         goto out;
     }
+    memset(Plo, 0, sizeof(int32_t) * (size_t)nB * (size_t)nA);
+    memset(Phi, 0, sizeof(int32_t) * (size_t)nB * (size_t)nA);
     for (int32_t b = 0; b < nB; ++b) { F[b] = 1; f[b] = S[b]; }
     for (int32_t a = 0; a < nA; ++a) { kmin[a] = 0; clo[a] = D[a]; chi[a] = 0; best[a] = INT32_MAX; }
 
@@ -143,19 +127,19 @@ int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *
                 int32_t g = r[w] < avail[a] ? r[w] : avail[a];
                 avail[a] -= g;
                 r[w] -= g;
-                /* Step II for this grant */
+                /* Step II for this grant: evict from the highest supply index */
                 if (kmin[a] >= 1) {
                     int32_t need = g;
-                    while (need > 0) {
-                        entry_t *top = &lo[a].e[lo[a].n - 1];
-                        int32_t t = top->cnt < need ? top->cnt : need;
-                        top->cnt -= t;
-                        f[top->b] += t;
+                    for (int32_t b2 = nB - 1; b2 >= 0 && need > 0; --b2) {
+                        int32_t *c = &Plo[(int64_t)b2 * nA + a];
+                        if (*c == 0) continue;
+                        int32_t t = *c < need ? *c : need;
+                        *c -= t;
+                        f[b2] += t;
                         need -= t;
-                        if (top->cnt == 0) lo[a].n -= 1;
                     }
                 }
-                if (push_entry(&hi[a], w, g) != 0) { rc = OR_ERR_NOMEM; goto out; }
+                Phi[(int64_t)w * nA + a] += g;
                 f[w] -= g;
                 clo[a] -= g;
                 chi[a] += g;
@@ -167,29 +151,22 @@ int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *
             if (in_bp[b] && r[b] > 0) F[b] += 1;
         for (int32_t a = 0; a < nA; ++a) {
             if (clo[a] == 0 && chi[a] > 0) {
+                /* the kmin cluster is empty (its matches were all evicted or
+                 * it held free copies): the clusters shift up */
                 kmin[a] += 1;
                 clo[a] = chi[a];
                 chi[a] = 0;
-                stack_t_ tmp = lo[a];
-                lo[a] = hi[a];
-                hi[a] = tmp;
-                hi[a].n = 0;
+                for (int32_t b = 0; b < nB; ++b) {
+                    Plo[(int64_t)b * nA + a] = Phi[(int64_t)b * nA + a];
+                    Phi[(int64_t)b * nA + a] = 0;
+                }
             }
         }
         if (mode & OR_MODE_CHECK) st->violations += or_ot_check(cb, nB, nA, F, f, kmin, clo, chi, NULL);
     }
 
-    memset(plan_lo, 0, sizeof(int32_t) * (size_t)nB * (size_t)nA);
-    memset(plan_hi, 0, sizeof(int32_t) * (size_t)nB * (size_t)nA);
-    for (int32_t a = 0; a < nA; ++a) {
-        if (kmin[a] >= 1)
-            for (int32_t i = 0; i < lo[a].n; ++i) plan_lo[(int64_t)lo[a].e[i].b * nA + a] += lo[a].e[i].cnt;
-        for (int32_t i = 0; i < hi[a].n; ++i) plan_hi[(int64_t)hi[a].e[i].b * nA + a] += hi[a].e[i].cnt;
-    }
 out:
-    if (lo) for (int32_t a = 0; a < nA; ++a) free(lo[a].e);
-    if (hi) for (int32_t a = 0; a < nA; ++a) free(hi[a].e);
-    free(lo); free(hi); free(r); free(ptr); free(prop); free(searching); free(in_bp);
+    free(r); free(ptr); free(prop); free(searching); free(in_bp);
     free(avail); free(best);
     return rc;
 }
