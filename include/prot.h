@@ -160,6 +160,47 @@ pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim
                                    size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Optimal transport (Sec. 4).                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes of pr_ot (0 if the sizes are invalid). */
+size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem);
+
+/*
+ * pr_ot -- additive approximation of optimal transport (Sec. 4): masses are
+ * scaled by theta = 4 max(n_sup, n_dem) / eps, supplies rounded down and
+ * demands rounded up to integer copy counts, and the matching algorithm of
+ * Sec. 2.2 (unbalanced, Sec. 3.3) runs on the copies with every free supply
+ * copy's dual raised to the largest among its siblings.  Copies are handled
+ * as clusters (Lemma 4.1: a vertex's copies take at most two dual values).
+ * The matched copies give mass(b,a) = copies / theta; a demand that received
+ * more than its mass gives the excess back from its highest-index supplier,
+ * and every supply's remainder is routed north-west-corner style (supplies
+ * ascending, demands ascending) into the remaining demand capacity.
+ *
+ *   C           n_sup x n_dem costs in [0,1] (rows = supplies B), ldc >= n_dem
+ *   supply      [n_sup] FP64 masses nu >= 0 summing to 1 (device)
+ *   demand      [n_dem] FP64 masses mu >= 0 summing to 1 (device)
+ *   plan_row, plan_col, plan_mass  [plan_cap] out: the plan as (supply,
+ *               demand, mass) triples, each pair at most once
+ *   plan_nnz    [1] out: number of triples (also written when > plan_cap,
+ *               which returns PR_ERR_CAPACITY)
+ *   y_sup       [n_sup] out: dual of the free copies of each supply (its
+ *               largest copy dual), units of eps
+ *   dem_kmin, dem_lo, dem_hi  [n_dem] out: each demand's copies have duals
+ *               -dem_kmin (dem_lo copies) and -dem_kmin - 1 (dem_hi copies)
+ *   cost        [1] out: sum of mass * C over the plan (FP64)
+ *   stats       host, may be NULL
+ * The phase loop is driven from the host (one counter read per round), so
+ * pr_ot synchronises `stream`.
+ */
+pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_sup, int32_t n_dem,
+                const double *supply, const double *demand, double eps, int64_t plan_cap,
+                int32_t *plan_row, int32_t *plan_col, double *plan_mass, int64_t *plan_nnz,
+                int32_t *y_sup, int32_t *dem_kmin, int32_t *dem_lo, int32_t *dem_hi, double *cost,
+                pr_stats *stats, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Differentiation of the assignment loss.                                   */
 /* ------------------------------------------------------------------------ */
 

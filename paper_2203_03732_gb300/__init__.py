@@ -16,7 +16,7 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["assign", "assign_batched", "assign_batched_points", "assign_backward",
+__all__ = ["assign", "assign_batched", "assign_batched_points", "assign_backward", "ot",
            "assignment_loss", "AssignLoss", "Workspace", "PrError"]
 
 PrError = _lib.PrError
@@ -291,3 +291,54 @@ def __getattr__(name):
 def assignment_loss(X, Y, eps: float):
     """Differentiable (batch,) loss for (batch, n, dim) FP32 CUDA point clouds."""
     return __getattr__("AssignLoss").apply(X, Y, eps)
+
+
+def ot(C, supply, demand, eps: float, *, plan_cap: int | None = None, ws: Workspace | None = None):
+    """Additive eps-approximate optimal transport (Sec. 4 of the paper).
+
+    C: (n_sup, n_dem) float32/float64 CUDA tensor of costs in [0, 1] (rows =
+    supplies); supply, demand: FP64 CUDA tensors of masses summing to 1.
+    Returns dict(plan_row, plan_col, plan_mass (the nnz plan triples), cost,
+    y_sup, dem_kmin, dem_lo, dem_hi (cluster duals, units of eps), stats)."""
+    torch = _torch()
+    L = _lib.load()
+    if not (C.is_cuda and supply.is_cuda and demand.is_cuda):
+        raise ValueError("C, supply and demand must be CUDA tensors")
+    if C.stride(1) != 1:
+        C = C.contiguous()
+    dt = {torch.float64: _lib.PR_F64, torch.float32: _lib.PR_F32}.get(C.dtype)
+    if dt is None:
+        raise TypeError("C must be float32 or float64")
+    nB, nA = C.shape
+    supply = supply.contiguous().to(torch.float64)
+    demand = demand.contiguous().to(torch.float64)
+    dev = C.device
+    need = L.pr_ot_workspace(nB, nA)
+    if need == 0:
+        raise PrError(_lib.PR_ERR_INVALID, "invalid sizes")
+    wsb = (ws or _workspace(dev)).get(need)
+    n = max(nB, nA)
+    if plan_cap is None:
+        # matched pairs are at most the supply copies (<= theta) and nB*nA;
+        # the fix-up adds at most nB + nA pairs
+        plan_cap = int(min(nB * nA, 4 * n / eps + 1) + nB + nA)
+    i32 = dict(dtype=torch.int32, device=dev)
+    out = dict(plan_row=torch.empty(plan_cap, **i32), plan_col=torch.empty(plan_cap, **i32),
+               plan_mass=torch.empty(plan_cap, dtype=torch.float64, device=dev),
+               plan_nnz=torch.zeros((), dtype=torch.int64, device=dev),
+               y_sup=torch.empty(nB, **i32), dem_kmin=torch.empty(nA, **i32),
+               dem_lo=torch.empty(nA, **i32), dem_hi=torch.empty(nA, **i32),
+               cost=torch.empty((), dtype=torch.float64, device=dev))
+    st = _lib.PrStats()
+    rc = L.pr_ot(C.data_ptr(), dt, C.stride(0), nB, nA, supply.data_ptr(), demand.data_ptr(),
+                 float(eps), plan_cap, out["plan_row"].data_ptr(), out["plan_col"].data_ptr(),
+                 out["plan_mass"].data_ptr(), out["plan_nnz"].data_ptr(), out["y_sup"].data_ptr(),
+                 out["dem_kmin"].data_ptr(), out["dem_lo"].data_ptr(), out["dem_hi"].data_ptr(),
+                 out["cost"].data_ptr(), ctypes.byref(st), wsb.data_ptr(), wsb.numel(),
+                 _stream_handle(torch, dev))
+    _lib.check(rc, "pr_ot")
+    nnz = int(out["plan_nnz"].item())
+    for k in ("plan_row", "plan_col", "plan_mass"):
+        out[k] = out[k][:nnz]
+    out["stats"] = st.as_dict()
+    return out

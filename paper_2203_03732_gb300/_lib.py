@@ -73,6 +73,9 @@ SIGNATURES = {
     "pr_assign_batched_points": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _i32, _vp, _dbl, _vp, _vp,
                                                 _vp, _vp, _vp, _vp, ctypes.POINTER(PrBatchedTune),
                                                 ctypes.POINTER(PrStats), _vp, _sz, _vp]),
+    "pr_ot_workspace": (_sz, [_i32, _i32]),
+    "pr_ot": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _vp, _vp, _dbl, _i64, _vp, _vp, _vp, _vp,
+                             _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_assign_backward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),
     "pr_set_kernel_events": (None, [_vp, _vp]),

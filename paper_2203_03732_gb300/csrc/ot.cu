@@ -1,0 +1,852 @@
+// ot.cu -- pr_ot: the optimal-transport form of Sec. 4 on one GB300.
+//
+// Sec. 4 scales the masses by theta = 4n/eps, rounds supplies down and
+// demands up, and runs the matching algorithm of Sec. 2.2 on the unit copies,
+// keeping every free supply copy's dual raised to the largest dual among its
+// siblings.  The copies are handled as clusters:
+//   supply b: F_b (dual of its free copies, the largest of its copies),
+//             f_b (free copies);
+//   demand a: keys k = -y in {kmin_a, kmin_a + 1} (Lemma 4.1): clo_a copies
+//             at kmin_a, chi_a at kmin_a + 1.
+// eps-feasibility of a free copy against a's kmin copies makes a's kmin
+// cluster the only one that can be admissible, and (a, b) is admissible iff
+// cbar(b,a) + kmin_a == F_b - 1 -- the assignment test with k(a) = kmin_a.
+//
+// Matched copy counts live in two dense planes [a][b]; plane sel[a] holds
+// a's matches at key kmin_a (its "lo" cluster), the other plane those at
+// kmin_a + 1.  When the lo cluster runs out (every match in it was evicted,
+// or it held a's free copies) the planes swap roles: the emptied plane is
+// all zero and becomes the new "hi" plane.
+//
+// One phase (B' = supply vertices with free copies), steps as kernels:
+//   k_ot_phase_start  r_b = f_b, flags, the free-copy total for the stop test
+//   round R: k_ot_propose  every searching b proposes (atomicMax on the
+//                          column word) to the lowest admissible a >= its
+//                          resume column with unmatched lo copies left;
+//            k_ot_grant    a's lowest proposer b gets g = min(r_b, avail_a)
+//                          copies; partners of matched lo copies are evicted,
+//                          highest supply index first (step II)
+//   k_ot_phase_end    F_b += 1 for b in B' left with unplaced copies (III b);
+//                     clusters shift up where the lo cluster is empty (III a)
+// The host runs the loop and reads one counter per round and per phase, so
+// pr_ot synchronises its stream.
+//
+// Plan and fix-up (a reading: the paper defers this part to another paper):
+// mass(b,a) = matched copies / theta; a demand that received more than mu_a
+// gives the excess back from its highest supply index; each supply's unsent
+// remainder is routed north-west-corner style (b ascending, a ascending) into
+// the remaining demand capacity.  The FP64 arithmetic of the fix-up follows
+// one fixed order (ascending b per demand, ascending a per supply, then the
+// north-west walk), so the masses are reproducible bit for bit.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "prot_internal.cuh"
+#include "quantise.cuh"
+#include "scan_common.cuh"
+
+namespace prot {
+namespace {
+
+constexpr int kOtThreads = 256;
+constexpr int kOtUnroll = 8;
+constexpr int kOtChunk = 32 * 8 * kOtUnroll;
+constexpr int kFlagSearching = 1, kFlagInBp = 2;
+
+struct OCtl {
+    WsHead head;
+    unsigned long long nfree;  // free supply copies at the phase start
+    int nprop;                 // proposals of the current round
+    int nnz;                   // plan entries from the matched copies
+    int n_nw;                  // north-west corner allocations
+    int n_extra;               // allocations on pairs without matched copies
+    long long bytes;
+};
+
+struct OLayout {
+    size_t ctl, cb, key, S, D, F, f, r, ptr, pa, flag, kmin, clo, chi, avail, sel, granted, prop;
+    size_t plane, nnz_a, off_a, trim_b, trim_t, q, rres, cnt_b, off_b, bsort_a, bsort_m, nw_flag,
+        nw_off, nw_b, nw_a, nw_t, total;
+    int ldq;
+    size_t plane_elems;
+};
+
+OLayout make_olayout(int nB, int nA) {
+    OLayout L;
+    Carver c;
+    L.ldq = (nA + 7) & ~7;
+    L.ctl = c.take<OCtl>(1);
+    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
+    L.key = c.take<uint16_t>(L.ldq);
+    L.S = c.take<int>(nB);
+    L.D = c.take<int>(nA);
+    L.F = c.take<int>(nB);
+    L.f = c.take<int>(nB);
+    L.r = c.take<int>(nB);
+    L.ptr = c.take<int>(nB);
+    L.pa = c.take<int>(nB);
+    L.flag = c.take<int>(nB);
+    L.kmin = c.take<int>(nA);
+    L.clo = c.take<int>(nA);
+    L.chi = c.take<int>(nA);
+    L.avail = c.take<int>(nA);
+    L.sel = c.take<int>(nA);
+    L.granted = c.take<int>(nA);
+    L.prop = c.take<unsigned long long>(nA);
+    L.plane_elems = (size_t)nA * (size_t)nB;
+    L.plane = c.take<int>(2 * L.plane_elems);
+    L.nnz_a = c.take<int>(nA);
+    L.off_a = c.take<int>((size_t)nA + 1);
+    L.trim_b = c.take<int>(nA);
+    L.trim_t = c.take<double>(nA);
+    L.q = c.take<double>(nA);
+    L.rres = c.take<double>(nB);
+    L.cnt_b = c.take<int>(nB);
+    L.off_b = c.take<int>((size_t)nB + 1);
+    L.bsort_a = L.plane;  // the count planes are dead once the plan is written
+    L.bsort_m = 0;
+    L.nw_flag = c.take<int>((size_t)nB + nA);
+    L.nw_off = c.take<int>((size_t)nB + nA + 1);
+    L.nw_b = c.take<int>((size_t)nB + nA);
+    L.nw_a = c.take<int>((size_t)nB + nA);
+    L.nw_t = c.take<double>((size_t)nB + nA);
+    L.total = c.total();
+    return L;
+}
+
+struct OParams {
+    OCtl *ctl;
+    const uint16_t *cb;
+    uint16_t *key;
+    int *S, *D, *F, *f, *r, *ptr, *pa, *flag;
+    int *kmin, *clo, *chi, *avail, *sel, *granted;
+    unsigned long long *prop;
+    int *plane;
+    size_t plane_elems;
+    int nB, nA, ldq;
+};
+
+__device__ __forceinline__ int *lo_plane(const OParams &p, int a) {
+    return p.plane + (size_t)p.sel[a] * p.plane_elems + (size_t)a * p.nB;
+}
+__device__ __forceinline__ int *hi_plane(const OParams &p, int a) {
+    return p.plane + (size_t)(p.sel[a] ^ 1) * p.plane_elems + (size_t)a * p.nB;
+}
+
+// S_b = floor(theta nu_b), D_a = ceil(theta mu_a) (Sec. 4), one FP64 product each.
+__global__ void k_ot_counts(const double *nu, const double *mu, int nB, int nA, double theta,
+                            int *S, int *D, WsHead *head) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nB + nA; i += stride) {
+        const bool sup = i < nB;
+        const double m = sup ? nu[i] : mu[i - nB];
+        const double v = sup ? floor(__dmul_rn(theta, m)) : ceil(__dmul_rn(theta, m));
+        if (!(m >= 0.0) || !(v <= 2147483647.0)) {
+            record_error(head, PR_ERR_INVALID);
+            continue;
+        }
+        if (sup) S[i] = (int)v;
+        else D[i - nB] = (int)v;
+    }
+}
+
+__global__ void k_ot_init(OParams p) {
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int b = t0; b < p.nB; b += stride) {
+        p.F[b] = 1;
+        p.f[b] = p.S[b];
+        p.r[b] = 0;
+        p.ptr[b] = 0;
+        p.pa[b] = -1;
+        p.flag[b] = 0;
+    }
+    for (int a = t0; a < p.ldq; a += stride) {
+        p.key[a] = a < p.nA ? 0 : kPadKey;
+        if (a >= p.nA) continue;
+        p.kmin[a] = 0;
+        p.clo[a] = p.D[a];
+        p.chi[a] = 0;
+        p.avail[a] = p.D[a];
+        p.sel[a] = 0;
+        p.granted[a] = 0;
+        p.prop[a] = word_of(0, -1);
+    }
+    uint4 *pl = reinterpret_cast<uint4 *>(p.plane);
+    const size_t n4 = (2 * p.plane_elems) / 4;
+    for (size_t i = t0; i < n4; i += stride) pl[i] = make_uint4(0, 0, 0, 0);
+    for (size_t i = n4 * 4 + t0; i < 2 * p.plane_elems; i += stride) p.plane[i] = 0;
+}
+
+__global__ void k_ot_ctl_init(OCtl *c) {
+    memset(c, 0, sizeof(OCtl));
+    c->head.magic = kWsMagic;
+}
+
+__global__ void k_ot_phase_start(OParams p) {
+    __shared__ unsigned long long part;
+    if (threadIdx.x == 0) part = 0;
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x) {
+        const int fb = p.f[b];
+        p.r[b] = fb;
+        p.flag[b] = fb > 0 ? (kFlagSearching | kFlagInBp) : 0;
+        p.ptr[b] = 0;
+        p.pa[b] = -1;
+        mine += (unsigned long long)fb;
+    }
+    atomicAdd(&part, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && part) atomicAdd(&p.ctl->nfree, part);
+}
+
+// Warp per searching supply vertex: the lowest a >= ptr with
+// cbar + kmin_a == F_b - 1 and avail_a > 0.
+__global__ void __launch_bounds__(kOtThreads) k_ot_propose(OParams p, unsigned R) {
+    __shared__ int props;
+    __shared__ unsigned long long sbytes;
+    if (threadIdx.x == 0) {
+        props = 0;
+        sbytes = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long bytes = 0;
+    for (int b = warp_g; b < p.nB; b += nwarps) {
+        if (!(p.flag[b] & kFlagSearching)) continue;
+        const uint32_t tgt = (uint32_t)(p.F[b] - 1);
+        const uint32_t t2 = tgt | (tgt << 16);
+        const uint16_t *row = p.cb + (size_t)b * p.ldq;
+        const int start = p.ptr[b];
+        int found = -1;
+        for (int c0 = start & ~7; c0 < p.ldq && found < 0; c0 += kOtChunk) {
+            uint4 sv[kOtUnroll];
+#pragma unroll
+            for (int u = 0; u < kOtUnroll; ++u) {
+                const int idx = c0 + u * 256 + lane * 8;
+                if (idx < p.ldq) {
+                    const uint4 c = ld_nc_na_v4(row + idx);
+                    const uint4 k = *reinterpret_cast<const uint4 *>(p.key + idx);
+                    sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
+                } else {
+                    sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+                }
+            }
+            bytes += 2ull * (unsigned long long)min(kOtChunk, p.ldq - c0);
+            for (int u = 0; u < kOtUnroll && found < 0; ++u) {
+                const int idx = c0 + u * 256 + lane * 8;
+                unsigned m = eq_mask(sv[u], t2);
+                const int lo = start - idx;
+                if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+                for (;;) {
+                    const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
+                    if (any == 0) break;
+                    const int L = __ffs(any) - 1;
+                    const int a = __shfl_sync(0xFFFFFFFFu, idx + __ffs(m) - 1, L);
+                    if (ld_relaxed_s32(p.avail + a) > 0) {
+                        found = a;
+                        break;
+                    }
+                    if (lane == L) m &= m - 1;
+                }
+            }
+        }
+        if (lane == 0) {
+            if (found >= 0) {
+                atomicMax(p.prop + found, word_of(R, b));
+                p.pa[b] = found;
+                p.ptr[b] = found;
+                atomicAdd(&props, 1);
+            } else {
+                p.flag[b] &= ~kFlagSearching;
+            }
+        }
+    }
+    if (lane == 0 && bytes) atomicAdd(&sbytes, bytes);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (props) atomicAdd(&p.ctl->nprop, props);
+        if (sbytes) atomicAdd((unsigned long long *)&p.ctl->bytes, sbytes);
+    }
+}
+
+// Warp per proposer: the winner of a takes g copies; the partners of matched
+// lo copies are evicted from the highest supply index down.
+__global__ void __launch_bounds__(kOtThreads) k_ot_grant(OParams p) {
+    const int lane = threadIdx.x & 31;
+    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->nprop = 0;  // read by the host already
+    for (int b = warp_g; b < p.nB; b += nwarps) {
+        const int a = p.pa[b];
+        if (a < 0) continue;
+        const bool win = row_of(p.prop[a]) == b;
+        int g = 0, need = 0;
+        if (lane == 0) {
+            p.pa[b] = -1;
+            if (win) {
+                const int av = p.avail[a];
+                const int rb = p.r[b];
+                g = rb < av ? rb : av;
+                p.avail[a] = av - g;
+                p.r[b] = rb - g;
+                if (rb - g == 0) p.flag[b] &= ~kFlagSearching;
+                p.clo[a] -= g;
+                p.chi[a] += g;
+                p.granted[a] = 1;
+                hi_plane(p, a)[b] += g;
+                atomicSub(p.f + b, g);
+                need = p.kmin[a] >= 1 ? g : 0;
+            }
+        }
+        need = __shfl_sync(0xFFFFFFFFu, need, 0);
+        if (need == 0) continue;
+        // step (II): evict `need` lo-cluster partners, highest supply index first
+        int *lo = lo_plane(p, a);
+        for (int top = p.nB - 1; top >= 0 && need > 0; top -= 32) {
+            const int b2 = top - lane;
+            const int c = b2 >= 0 ? lo[b2] : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int before = incl - c;
+            int t = need - before;
+            t = t < 0 ? 0 : (t > c ? c : t);
+            if (t > 0) {
+                lo[b2] = c - t;
+                atomicAdd(p.f + b2, t);
+            }
+            const int chunk_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            need -= chunk_total < need ? chunk_total : need;
+        }
+    }
+}
+
+__global__ void k_ot_phase_end(OParams p) {
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int b = t0; b < p.nB; b += stride)
+        if ((p.flag[b] & kFlagInBp) && p.r[b] > 0) p.F[b] += 1;  // step (III b)
+    for (int a = t0; a < p.nA; a += stride) {
+        if (!p.granted[a]) continue;
+        p.granted[a] = 0;
+        if (p.clo[a] == 0 && p.chi[a] > 0) {  // step (III a): clusters shift up
+            const int k = p.kmin[a] + 1;
+            p.kmin[a] = k;
+            p.key[a] = (uint16_t)k;
+            p.clo[a] = p.chi[a];
+            p.chi[a] = 0;
+            p.sel[a] ^= 1;
+        }
+        p.avail[a] = p.clo[a];
+    }
+    if (t0 == 0) p.ctl->nfree = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Plan and fix-up
+// ---------------------------------------------------------------------------
+struct FixParams {
+    OParams o;
+    const double *nu, *mu;
+    double theta;
+    int *nnz_a, *off_a, *trim_b;
+    double *trim_t, *q, *rres;
+    int *cnt_b, *off_b, *bsort_a;
+    int *nw_b, *nw_a;
+    double *nw_t;
+    int *plan_row, *plan_col;
+    double *plan_mass;
+    long long plan_cap;
+};
+
+// Warp per demand a: nonzero count, the trim of its highest supplier, and the
+// remaining capacity q_a = max(0, mu_a - received), sums in ascending b.
+__global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
+    const OParams &p = fp.o;
+    const int lane = threadIdx.x & 31;
+    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int a = warp_g; a < p.nA; a += nwarps) {
+        const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
+        int nnz = 0, last = -1;
+        double recv = 0.0, before_last = 0.0, m_last = 0.0;
+        for (int b0 = 0; b0 < p.nB; b0 += 32) {
+            const int b = b0 + lane;
+            const int c = b < p.nB ? lo[b] + hi[b] : 0;
+            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (!nz) continue;
+            nnz += __popc(nz);
+            const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
+            // lane order = ascending b: fold the chunk's masses in that order
+            for (unsigned w = nz; w; w &= w - 1) {
+                const int L = __ffs(w) - 1;
+                const double mi = __shfl_sync(0xFFFFFFFFu, m, L);
+                before_last = recv;
+                m_last = mi;
+                recv = __dadd_rn(recv, mi);
+                last = b0 + L;
+            }
+        }
+        if (lane == 0) {
+            fp.nnz_a[a] = nnz;
+            const double excess = __dsub_rn(recv, fp.mu[a]);
+            int tb = -1;
+            double tt = 0.0, r2 = recv;
+            if (excess > 0.0 && last >= 0) {
+                // every positive mass is >= 1/theta > excess: one trim, on the
+                // highest supplier, which is also the last term of the sum
+                tb = last;
+                tt = m_last < excess ? m_last : excess;
+                r2 = __dadd_rn(before_last, __dsub_rn(m_last, tt));
+            }
+            fp.trim_b[a] = tb;
+            fp.trim_t[a] = tt;
+            const double qa = __dsub_rn(fp.mu[a], r2);
+            fp.q[a] = qa < 0.0 ? 0.0 : qa;
+        }
+    }
+}
+
+// One CTA: exclusive prefix sums of n counts (out[n] = total).
+__global__ void k_prefix(const int *cnt, int n, int *out) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? cnt[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const int w = lane < nw ? warp_tot[lane] : 0;
+            int z = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                if (lane >= o) z += y;
+            }
+            if (lane < nw) warp_tot[lane] = z - w;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + warp_tot[warp] + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += warp_tot[warp] + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// Warp per demand a: write a's plan entries (b ascending) at off_a[a]; count
+// the entries of every supply row.
+__global__ void __launch_bounds__(kOtThreads) k_fix_write(FixParams fp) {
+    const OParams &p = fp.o;
+    const int lane = threadIdx.x & 31;
+    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int a = warp_g; a < p.nA; a += nwarps) {
+        const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
+        int pos = fp.off_a[a];
+        const int tb = fp.trim_b[a];
+        for (int b0 = 0; b0 < p.nB; b0 += 32) {
+            const int b = b0 + lane;
+            const int c = b < p.nB ? lo[b] + hi[b] : 0;
+            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (!nz) continue;
+            if (c) {
+                const int k = pos + __popc(nz & ((1u << lane) - 1));
+                double m = __ddiv_rn((double)c, fp.theta);
+                if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
+                if (k < fp.plan_cap) {
+                    fp.plan_row[k] = b;
+                    fp.plan_col[k] = a;
+                    fp.plan_mass[k] = m;
+                }
+                atomicAdd(fp.cnt_b + b, 1);
+            }
+            pos += __popc(nz);
+        }
+    }
+}
+
+// Thread per entry: scatter the entry index into its supply row's segment.
+__global__ void k_fix_bscatter(FixParams fp, int nnz, int *fill) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int b = fp.plan_row[k];
+        fp.bsort_a[fp.off_b[b] + atomicAdd(fill + b, 1)] = k;
+    }
+}
+
+// Thread per supply b: its entries in ascending a (insertion sort of the
+// row's small segment), then rres_b = max(0, nu_b - sent_b).
+__global__ void k_fix_supply(FixParams fp) {
+    const OParams &p = fp.o;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x) {
+        const int s = fp.off_b[b], e = fp.off_b[b + 1];
+        int *seg = fp.bsort_a + s;
+        for (int i = 1; i < e - s; ++i) {
+            const int v = seg[i];
+            const int av = fp.plan_col[v];
+            int j = i - 1;
+            while (j >= 0 && fp.plan_col[seg[j]] > av) {
+                seg[j + 1] = seg[j];
+                --j;
+            }
+            seg[j + 1] = v;
+        }
+        double sent = 0.0;
+        for (int i = 0; i < e - s; ++i) sent = __dadd_rn(sent, fp.plan_mass[seg[i]]);
+        const double rr = __dsub_rn(fp.nu[b], sent);
+        fp.rres[b] = rr < 0.0 ? 0.0 : rr;
+    }
+}
+
+// One thread: the north-west corner over the residuals (b ascending, a
+// ascending); residuals staged in shared memory when they fit.
+__global__ void k_fix_nw(FixParams fp, int use_smem, OCtl *ctl) {
+    extern __shared__ double sm[];
+    const OParams &p = fp.o;
+    double *rr = use_smem ? sm : fp.rres;
+    double *qq = use_smem ? sm + p.nB : fp.q;
+    if (use_smem) {
+        for (int i = threadIdx.x; i < p.nB; i += blockDim.x) rr[i] = fp.rres[i];
+        for (int i = threadIdx.x; i < p.nA; i += blockDim.x) qq[i] = fp.q[i];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    int i = 0, j = 0, n = 0;
+    while (i < p.nB && j < p.nA) {
+        if (rr[i] <= 0.0) {
+            ++i;
+            continue;
+        }
+        if (qq[j] <= 0.0) {
+            ++j;
+            continue;
+        }
+        const double t = rr[i] < qq[j] ? rr[i] : qq[j];
+        fp.nw_b[n] = i;
+        fp.nw_a[n] = j;
+        fp.nw_t[n] = t;
+        ++n;
+        rr[i] = __dsub_rn(rr[i], t);
+        qq[j] = __dsub_rn(qq[j], t);
+    }
+    ctl->n_nw = n;
+}
+
+// Thread per north-west allocation: add it to the matched entry of (b, a)
+// (binary search in a's segment, ascending b), or flag it as a new entry.
+__global__ void k_fix_merge(FixParams fp, OCtl *ctl, int *flag) {
+    const int n = ctl->n_nw;
+    const int total = fp.o.nB + fp.o.nA;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        int fl = 0;
+        if (k < n) {
+            const int b = fp.nw_b[k], a = fp.nw_a[k];
+            int lo = fp.off_a[a], hi = fp.off_a[a + 1] - 1, at = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int bm = fp.plan_row[mid];
+                if (bm == b) {
+                    at = mid;
+                    break;
+                }
+                if (bm < b) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (at >= 0) fp.plan_mass[at] = __dadd_rn(fp.plan_mass[at], fp.nw_t[k]);
+            else fl = 1;
+        }
+        flag[k] = fl;
+    }
+}
+
+// New pairs go after the matched entries, in north-west order.
+__global__ void k_fix_append(FixParams fp, OCtl *ctl, const int *flag, const int *off) {
+    const int n = ctl->n_nw;
+    const int nnz = fp.off_a[fp.o.nA];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        const long long pos = (long long)nnz + off[k];
+        if (pos < fp.plan_cap) {
+            fp.plan_row[pos] = fp.nw_b[k];
+            fp.plan_col[pos] = fp.nw_a[k];
+            fp.plan_mass[pos] = fp.nw_t[k];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_extra = off[fp.o.nB + fp.o.nA];
+}
+
+// One CTA: cost = sum mass * c over the plan, fixed-order tree reduction.
+template <class T>
+__global__ void __launch_bounds__(1024)
+k_fix_cost(FixParams fp, const T *C, long long ldc, OCtl *ctl, int64_t *plan_nnz, double *cost) {
+    __shared__ double part[1024];
+    const int nnz = fp.off_a[fp.o.nA] + ctl->n_extra;
+    const int lim = nnz < fp.plan_cap ? nnz : (int)fp.plan_cap;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < lim; k += blockDim.x)
+        acc = __dadd_rn(acc, __dmul_rn(fp.plan_mass[k], (double)C[(long long)fp.plan_row[k] * ldc + fp.plan_col[k]]));
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *cost = part[0];
+        *plan_nnz = nnz;
+    }
+}
+
+__global__ void k_ot_duals(OParams p, int *y_sup, int *dem_kmin, int *dem_lo, int *dem_hi) {
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int b = t0; b < p.nB; b += stride) y_sup[b] = p.F[b];
+    for (int a = t0; a < p.nA; a += stride) {
+        dem_kmin[a] = p.kmin[a];
+        dem_lo[a] = p.clo[a];
+        dem_hi[a] = p.chi[a];
+    }
+}
+
+__global__ void k_zero_int(int *x, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0;
+}
+
+}  // namespace
+}  // namespace prot
+
+using namespace prot;
+
+extern "C" size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem) {
+    if (n_sup < 1 || n_dem < 1 || n_sup > (1 << 24) || n_dem > (1 << 24)) return 0;
+    if ((size_t)n_sup * (size_t)n_dem > ((size_t)1 << 31) - 1) return 0;
+    return make_olayout(n_sup, n_dem).total;
+}
+
+extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_sup, int32_t n_dem,
+                           const double *supply, const double *demand, double eps,
+                           int64_t plan_cap, int32_t *plan_row, int32_t *plan_col,
+                           double *plan_mass, int64_t *plan_nnz, int32_t *y_sup,
+                           int32_t *dem_kmin, int32_t *dem_lo, int32_t *dem_hi, double *cost,
+                           pr_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+    if (!C || !supply || !demand || !plan_row || !plan_col || !plan_mass || !plan_nnz || !y_sup ||
+        !dem_kmin || !dem_lo || !dem_hi || !cost)
+        return fail(PR_ERR_INVALID, "pr_ot: NULL pointer argument");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_ot: bad dtype");
+    if (n_sup < 1 || n_dem < 1 || n_sup > (1 << 24) || n_dem > (1 << 24) ||
+        (size_t)n_sup * (size_t)n_dem > ((size_t)1 << 31) - 1)
+        return fail(PR_ERR_INVALID, "pr_ot: need 1 <= n_sup, n_dem and n_sup * n_dem < 2^31");
+    if (ldc < n_dem) return fail(PR_ERR_INVALID, "pr_ot: ldc < n_dem");
+    if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
+        return fail(PR_ERR_INVALID, "pr_ot: need 0 < eps < 1 and floor(1/eps) <= 32766");
+    if (plan_cap < 1) return fail(PR_ERR_INVALID, "pr_ot: plan_cap must be >= 1");
+    const OLayout L = make_olayout(n_sup, n_dem);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
+        return fail(PR_ERR_WORKSPACE, "pr_ot: workspace NULL, not 256-byte aligned or < %zu bytes", L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    const int nB = n_sup, nA = n_dem;
+    const int n = nB > nA ? nB : nA;
+    const double theta = (4.0 * (double)n) / eps;
+
+    OParams p;
+    p.ctl = (OCtl *)(w + L.ctl);
+    p.cb = (const uint16_t *)(w + L.cb);
+    p.key = (uint16_t *)(w + L.key);
+    p.S = (int *)(w + L.S);
+    p.D = (int *)(w + L.D);
+    p.F = (int *)(w + L.F);
+    p.f = (int *)(w + L.f);
+    p.r = (int *)(w + L.r);
+    p.ptr = (int *)(w + L.ptr);
+    p.pa = (int *)(w + L.pa);
+    p.flag = (int *)(w + L.flag);
+    p.kmin = (int *)(w + L.kmin);
+    p.clo = (int *)(w + L.clo);
+    p.chi = (int *)(w + L.chi);
+    p.avail = (int *)(w + L.avail);
+    p.sel = (int *)(w + L.sel);
+    p.granted = (int *)(w + L.granted);
+    p.prop = (unsigned long long *)(w + L.prop);
+    p.plane = (int *)(w + L.plane);
+    p.plane_elems = L.plane_elems;
+    p.nB = nB;
+    p.nA = nA;
+    p.ldq = L.ldq;
+
+    const DeviceInfo &di = device_info();
+    const int g1 = di.sms * 4;
+    k_ot_ctl_init<<<1, 1, 0, st>>>(p.ctl);
+    PR_CUDA(cudaGetLastError());
+    k_ot_counts<<<g1, 256, 0, st>>>(supply, demand, nB, nA, theta, p.S, p.D, &p.ctl->head);
+    PR_CUDA(cudaGetLastError());
+    k_ot_init<<<g1 * 4, 256, 0, st>>>(p);
+    PR_CUDA(cudaGetLastError());
+    {
+        const long long groups = (long long)nB * (L.ldq >> 3);
+        const long long want = groups / 256 + 1;
+        const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
+        const float inv_eps = (float)(1.0 / eps);
+        if (dt == PR_F64)
+            k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, nB, nA, L.ldq, eps, inv_eps,
+                                                      (uint16_t *)p.cb, &p.ctl->head);
+        else
+            k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, nB, nA, L.ldq, eps, inv_eps,
+                                                     (uint16_t *)p.cb, &p.ctl->head);
+        PR_CUDA(cudaGetLastError());
+    }
+    OCtl h;
+    PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: invalid costs or masses");
+    // S = total supply copies; T = floor(eps * S) (Sec. 3.3 on the copy instance)
+    std::vector<int> hS(nB);
+    PR_CUDA(cudaMemcpyAsync(hS.data(), p.S, sizeof(int) * nB, cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    long long S_total = 0;
+    for (int b = 0; b < nB; ++b) S_total += hS[b];
+    const long long T = (long long)floor(eps * (double)S_total);
+    const long long K = (long long)floor(1.0 / eps);
+    const long long cap = (S_total * (2 * K + 3)) / (T + 1) + 1;
+
+    const int gw = di.sms * 8;  // warps-per-row kernels: grid of 256-thread CTAs
+    long long phases = 0, rounds = 0;
+    unsigned R = 0;
+    long long free_at_stop = 0;
+    pr_status rc = PR_OK;
+    for (;;) {
+        k_ot_phase_start<<<g1, 256, 0, st>>>(p);
+        PR_CUDA(cudaGetLastError());
+        unsigned long long nfree = 0;
+        PR_CUDA(cudaMemcpyAsync(&nfree, &p.ctl->nfree, sizeof(nfree), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        if ((long long)nfree <= T) {
+            free_at_stop = (long long)nfree;
+            break;
+        }
+        if (phases >= cap) {
+            free_at_stop = (long long)nfree;
+            rc = fail(PR_ERR_NO_CONVERGENCE, "pr_ot: phase cap reached");
+            break;
+        }
+        ++phases;
+        for (;;) {
+            ++R;
+            k_ot_propose<<<gw, kOtThreads, 0, st>>>(p, R);
+            PR_CUDA(cudaGetLastError());
+            int nprop = 0;
+            PR_CUDA(cudaMemcpyAsync(&nprop, &p.ctl->nprop, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PR_CUDA(cudaStreamSynchronize(st));
+            if (nprop == 0) break;
+            ++rounds;
+            k_ot_grant<<<gw, kOtThreads, 0, st>>>(p);
+            PR_CUDA(cudaGetLastError());
+        }
+        k_ot_phase_end<<<g1, 256, 0, st>>>(p);
+        PR_CUDA(cudaGetLastError());
+    }
+    if (rc != PR_OK) return rc;
+
+    // plan and fix-up
+    FixParams fp;
+    fp.o = p;
+    fp.nu = supply;
+    fp.mu = demand;
+    fp.theta = theta;
+    fp.nnz_a = (int *)(w + L.nnz_a);
+    fp.off_a = (int *)(w + L.off_a);
+    fp.trim_b = (int *)(w + L.trim_b);
+    fp.trim_t = (double *)(w + L.trim_t);
+    fp.q = (double *)(w + L.q);
+    fp.rres = (double *)(w + L.rres);
+    fp.cnt_b = (int *)(w + L.cnt_b);
+    fp.off_b = (int *)(w + L.off_b);
+    fp.bsort_a = (int *)(w + L.bsort_a);
+    fp.nw_b = (int *)(w + L.nw_b);
+    fp.nw_a = (int *)(w + L.nw_a);
+    fp.nw_t = (double *)(w + L.nw_t);
+    fp.plan_row = plan_row;
+    fp.plan_col = plan_col;
+    fp.plan_mass = plan_mass;
+    fp.plan_cap = plan_cap;
+    k_fix_demand<<<gw, kOtThreads, 0, st>>>(fp);
+    PR_CUDA(cudaGetLastError());
+    k_prefix<<<1, 1024, 0, st>>>(fp.nnz_a, nA, fp.off_a);
+    PR_CUDA(cudaGetLastError());
+    int nnz = 0;
+    PR_CUDA(cudaMemcpyAsync(&nnz, fp.off_a + nA, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    if (nnz > plan_cap) {
+        const long long v = nnz;
+        PR_CUDA(cudaMemcpyAsync(plan_nnz, &v, sizeof(v), cudaMemcpyHostToDevice, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        return fail(PR_ERR_CAPACITY, "pr_ot: %d plan entries exceed plan_cap", nnz);
+    }
+    k_zero_int<<<g1, 256, 0, st>>>(fp.cnt_b, nB);
+    k_fix_write<<<gw, kOtThreads, 0, st>>>(fp);
+    PR_CUDA(cudaGetLastError());
+    k_prefix<<<1, 1024, 0, st>>>(fp.cnt_b, nB, fp.off_b);
+    k_zero_int<<<g1, 256, 0, st>>>(fp.cnt_b, nB);
+    k_fix_bscatter<<<g1, 256, 0, st>>>(fp, nnz, fp.cnt_b);
+    k_fix_supply<<<(nB + 255) / 256, 256, 0, st>>>(fp);
+    PR_CUDA(cudaGetLastError());
+    {
+        const size_t need = (size_t)(nB + nA) * sizeof(double);
+        const int use_smem = need <= (size_t)di.max_smem_optin ? 1 : 0;
+        if (use_smem)
+            PR_CUDA(cudaFuncSetAttribute(k_fix_nw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+        k_fix_nw<<<1, 256, use_smem ? need : 0, st>>>(fp, use_smem, p.ctl);
+        PR_CUDA(cudaGetLastError());
+    }
+    {
+        int *flag = (int *)(w + L.nw_flag), *off = (int *)(w + L.nw_off);
+        k_fix_merge<<<g1, 256, 0, st>>>(fp, p.ctl, flag);
+        PR_CUDA(cudaGetLastError());
+        k_prefix<<<1, 1024, 0, st>>>(flag, nB + nA, off);
+        k_fix_append<<<g1, 256, 0, st>>>(fp, p.ctl, flag, off);
+        PR_CUDA(cudaGetLastError());
+    }
+    if (dt == PR_F64)
+        k_fix_cost<double><<<1, 1024, 0, st>>>(fp, (const double *)C, ldc, p.ctl, plan_nnz, cost);
+    else
+        k_fix_cost<float><<<1, 1024, 0, st>>>(fp, (const float *)C, ldc, p.ctl, plan_nnz, cost);
+    PR_CUDA(cudaGetLastError());
+    k_ot_duals<<<g1, 256, 0, st>>>(p, y_sup, dem_kmin, dem_lo, dem_hi);
+    PR_CUDA(cudaGetLastError());
+    PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    if ((long long)nnz + h.n_extra > plan_cap)
+        return fail(PR_ERR_CAPACITY, "pr_ot: %lld plan entries exceed plan_cap", (long long)nnz + h.n_extra);
+    if (stats) {
+        stats->phases = phases;
+        stats->rounds = rounds;
+        stats->bytes_scanned = h.bytes;
+        stats->rows_scanned = 0;
+        stats->free_at_stop = (int32_t)free_at_stop;
+        stats->threshold = (int32_t)T;
+    }
+    if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
+    return PR_OK;
+}

@@ -1,0 +1,87 @@
+"""GPU parity of pr_ot against the OT oracle: cluster duals, phase and round
+counts bit-exact; the plan (masses after the fix-up) bit-exact; FP64 cost
+within 1e-12 relative; plan feasibility."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ot as O
+from paper_2203_03732_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def prot():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_03732_gb300 import build
+    build.build()
+    import paper_2203_03732_gb300 as P
+    return P
+
+
+def gpu_ot(P, C, nu, mu, eps):
+    import torch
+    r = P.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), eps)
+    nB, nA = C.shape
+    dense = np.zeros((nB, nA))
+    rows, cols = r["plan_row"].cpu().numpy(), r["plan_col"].cpu().numpy()
+    assert len(set(zip(rows.tolist(), cols.tolist()))) == rows.size  # each pair once
+    dense[rows, cols] = r["plan_mass"].cpu().numpy()
+    return r, dense
+
+
+def assert_ot_parity(r, dense, ref):
+    assert np.array_equal(r["y_sup"].cpu().numpy(), ref["F"])
+    assert np.array_equal(r["dem_kmin"].cpu().numpy(), ref["kmin"])
+    assert np.array_equal(r["dem_lo"].cpu().numpy(), ref["clo"])
+    assert np.array_equal(r["dem_hi"].cpu().numpy(), ref["chi"])
+    st = r["stats"]
+    assert st["phases"] == ref["stats"]["phases"]
+    assert st["rounds"] == ref["stats"]["rounds"]
+    assert st["free_at_stop"] == ref["stats"]["free_at_stop"]
+    assert st["threshold"] == ref["T"]
+    assert np.array_equal(dense, ref["mass"])
+    c = float(r["cost"].cpu())
+    assert abs(c - ref["cost"]) <= 1e-12 * abs(ref["cost"])
+
+
+@pytest.mark.parametrize("nB,nA,eps", [(20, 25, 0.1), (64, 64, 0.05), (300, 257, 0.05),
+                                       (1000, 1200, 0.02), (2100, 2000, 0.1), (1, 1, 0.5)])
+def test_ot_matches_oracle(prot, nB, nA, eps):
+    C, nu, mu = W.ot_euclid_2d(nB, nA, nB + nA)
+    r, dense = gpu_ot(prot, C, nu, mu, eps)
+    ref = O.ot(C, nu, mu, eps)
+    assert_ot_parity(r, dense, ref)
+    assert np.abs(dense.sum(1) - nu).max() <= 1e-12
+    assert (dense.sum(0) - mu).max() <= 1e-12
+
+
+def test_ot_zero_masses(prot):
+    C, nu, mu = W.ot_euclid_2d(40, 50, 3)
+    nu = nu.copy()
+    nu[[1, 7]] = 0.0
+    nu /= nu.sum()
+    mu = mu.copy()
+    mu[[0, 4, 49]] = 0.0
+    mu /= mu.sum()
+    r, dense = gpu_ot(prot, C, nu, mu, 0.05)
+    assert_ot_parity(r, dense, O.ot(C, nu, mu, 0.05))
+
+
+def test_ot_full_size(prot):
+    """The 10,000 x 10,000 Dirichlet(1) workload at eps = 0.05, compared in full."""
+    C, nu, mu = W.ot_euclid_2d(10000, 10000, 0)
+    r, dense = gpu_ot(prot, C, nu, mu, 0.05)
+    ref = O.ot(C, nu, mu, 0.05)
+    assert_ot_parity(r, dense, ref)
+
+
+def test_ot_bad_masses(prot):
+    import torch
+    C, nu, mu = W.ot_euclid_2d(10, 10, 1)
+    nu[3] = -0.1
+    with pytest.raises(prot.PrError):
+        prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.1)
