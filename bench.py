@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the eps sweep, batched, autograd and OT measurements")
     return ap.parse_args()
 
 
@@ -216,6 +218,121 @@ def run_e2e(a, torch, prot, C_pin, Cd, ws, out, stream, ref):
             "d2h_bytes_per_step": int(a.n * 4 + 8)}
 
 
+def timed(torch, stream, fn, reps):
+    """Device time of fn() per call: CUDA events around `reps` calls."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_extras(a, torch, prot, W, dev, stream):
+    """The other measurements of the headline metric, each bounded in time."""
+    import numpy as np
+    ex = {}
+    # eps sweep of the n=10k single solve
+    C = torch.from_numpy(W.assignment_euclid_2d(a.n, a.seed)).to(dev)
+    ws = prot.Workspace(dev)
+    sweep = {}
+    for eps in (0.1, 0.005):
+        r = prot.assign(C, eps, ws=ws)
+        out = {k: v for k, v in r.items() if k != "stats"}
+        prot.assign(C, eps, ws=ws, sync=False, out=out)
+        ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out), 10)
+        sweep[str(eps)] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+                           "bytes_scanned": r["stats"]["bytes_scanned"]}
+    ex["assign_eps_sweep"] = sweep
+    del C
+
+    # batched: 512 problems, n_i uniform in [64, 2048], 3-D points, sq. Euclidean, eps 0.01
+    sizes = W.batched_sizes(512, 64, 2048, seed=0)
+    XA, XB, off = W.batched_points_3d(sizes, seed=0)
+    XAd, XBd = torch.from_numpy(XA).to(dev), torch.from_numpy(XB).to(dev)
+    wsb = prot.Workspace(dev)
+    res = prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb)
+    outb = {k: v for k, v in res.items() if k != "stats"}
+    ms_pts = timed(torch, stream, lambda: prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb,
+                                                                      sync=False, out=outb), 3)
+    # the same problems as FP32 cost matrices: one batched launch vs one launch per problem
+    mats = []
+    for i in range(len(sizes)):
+        xa, xb = XAd[off[i]:off[i + 1]], XBd[off[i]:off[i + 1]]
+        d = ((xb[:, None, :] - xa[None, :, :]) ** 2).sum(-1)
+        mats.append((d / d.max()).contiguous())
+    packed = torch.cat([m.reshape(-1) for m in mats])
+    resm = prot.assign_batched(packed, sizes, 0.01, ws=wsb)
+    outm = {k: v for k, v in resm.items() if k != "stats"}
+    ms_mat = timed(torch, stream, lambda: prot.assign_batched(packed, sizes, 0.01, ws=wsb, sync=False,
+                                                               out=outm), 3)
+    wsp = prot.Workspace(dev)
+    outs = [None] * len(mats)
+
+    def plain():
+        for i, m in enumerate(mats):
+            r = prot.assign(m, 0.01, ws=wsp, sync=False, out=outs[i])
+            outs[i] = {k: v for k, v in r.items() if k != "stats"}
+    plain()
+    ms_plain = timed(torch, stream, plain, 1)
+    P = len(sizes)
+    ex["batched"] = {"workload": "512 problems, n_i ~ U{64..2048}, 3-D uniform points, squared Euclidean / max, eps=0.01",
+                     "problems_per_s_points": P / (ms_pts * 1e-3),
+                     "problems_per_s_matrix": P / (ms_mat * 1e-3),
+                     "problems_per_s_plain": P / (ms_plain * 1e-3),
+                     "ms_points": ms_pts, "ms_matrix": ms_mat, "ms_plain_512_launches": ms_plain,
+                     "speedup_vs_plain": ms_plain / ms_mat,
+                     "phases_total": int(res["stats"]["phases"]), "bytes_scanned": res["stats"]["bytes_scanned"]}
+    del packed, mats, outs
+
+    # autograd: 64 pairs, n = 4096, d = 3, N(0,1), squared Euclidean, eps 0.01
+    X, Y = W.cloud_pairs_normal(64, 4096, 3, seed=0)
+    Xd = torch.from_numpy(X).to(dev).requires_grad_(True)
+    Yd = torch.from_numpy(Y).to(dev).requires_grad_(True)
+
+    def fwd_bwd():
+        Xd.grad = None
+        Yd.grad = None
+        prot.assignment_loss(Xd, Yd, 0.01).sum().backward()
+    fwd_bwd()
+    ms_ag = timed(torch, stream, fwd_bwd, 2)
+    Xp, Yp = Xd.detach(), Yd.detach()
+    costs = []
+    for p in range(64):
+        d = ((Xp[p][:, None, :] - Yp[p][None, :, :]) ** 2).sum(-1)
+        costs.append((d / d.max()).contiguous())
+    wsa = prot.Workspace(dev)
+    g1 = torch.ones(1, device=dev)
+
+    def plain_pairs():
+        for p in range(64):
+            r = prot.assign(costs[p], 0.01, ws=wsa, sync=False)
+            prot.assign_backward(r["row_to_col"], Xp[p:p + 1], Yp[p:p + 1], g1)
+    plain_pairs()
+    ms_ag_plain = timed(torch, stream, plain_pairs, 1)
+    ex["autograd"] = {"workload": "64 pairs, n=4096, d=3, N(0,1), squared Euclidean, eps=0.01",
+                      "ms_forward_backward": ms_ag, "ms_plain_64x(assign+backward)": ms_ag_plain,
+                      "speedup_vs_plain": ms_ag_plain / ms_ag}
+    del costs
+
+    # OT: 10k x 10k, Dirichlet(1) masses, Euclidean / max, eps 0.05
+    Co, nu, mu = W.ot_euclid_2d(a.n, a.n, 0)
+    Cod, nud, mud = (torch.from_numpy(x).to(dev) for x in (Co, nu, mu))
+    wso = prot.Workspace(dev)
+    r = prot.ot(Cod, nud, mud, 0.05, ws=wso)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        r = prot.ot(Cod, nud, mud, 0.05, ws=wso)
+    ms_ot = (time.perf_counter() - t0) * 1e3 / reps  # pr_ot synchronises: host clock
+    ex["ot"] = {"workload": "OT 10k x 10k, 2-D uniform, Euclidean / max, Dirichlet(1) masses, eps=0.05",
+                "ms": ms_ot, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+                "plan_nnz": int(r["plan_row"].numel()), "cost": float(r["cost"].cpu())}
+    return ex
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -300,6 +417,10 @@ def main():
             dist.destroy_process_group()
         return
 
+    extras = None
+    if not a.no_extras and world == 1:
+        extras = run_extras(a, torch, prot, W, dev, stream)
+
     peak, peak_src = measured_peak()
     bytes_per_launch = float(st["bytes_scanned"])
     achieved = bytes_per_launch / (k_avg * 1e-3) / 1e9
@@ -326,6 +447,7 @@ def main():
         "solver": {"phases": st["phases"], "rounds": st["rounds"], "rows_scanned": st["rows_scanned"],
                    "free_at_stop": st["free_at_stop"], "threshold": st["threshold"],
                    "cost": float(ref["cost"].cpu()), "phase_loop_ms": k_avg},
+        "extras": extras,
     }
     print(json.dumps(line), flush=True)
     if dist:
