@@ -227,6 +227,30 @@ pr_status pr_assign_backward(const int32_t *row_to_col, const float *X, const fl
                              float *grad_X, float *grad_Y, float *grad_C, void *stream);
 
 /*
+ * pr_assign_noalloc -- pr_assign for callers that cannot allocate device
+ * memory: code running where cudaMalloc is not allowed or not wanted (while
+ * a stream is being captured into a CUDA graph, inside a host application
+ * that forbids device allocations after start-up, or in a latency-critical
+ * loop that must not enter the allocator), and callers with no way to keep
+ * a workspace between calls.  It computes exactly what pr_assign computes.
+ * The paper has no counterpart: this is a packaging of the same solve.
+ *
+ * Instead of a caller workspace it uses one device array of 2.25 MiB built
+ * into the library; every GPU that loads the library holds that array until
+ * the process exits.  Limits: n_rows <= n_cols <= 1024 (larger sizes return
+ * PR_ERR_INVALID with a message).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls on a device
+ * share the array and each call reinitialises what it uses, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  No memory is allocated or freed by this call.  Other arguments and
+ * errors as pr_assign (stats non-NULL makes the call synchronous).
+ */
+pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int32_t n_cols,
+                            double eps, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                            int32_t *y_col, double *cost, pr_stats *stats, void *stream);
+
+/*
  * Synchronise `stream` and return the device-side status recorded in a
  * workspace by the last call that used it (PR_OK if none).  For callers that
  * pass stats == NULL.  `ws` must be a workspace of that call.

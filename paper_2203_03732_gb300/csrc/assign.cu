@@ -36,6 +36,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "prot_internal.cuh"
 #include "scan_common.cuh"
 #include "quantise.cuh"
@@ -798,6 +800,167 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
         stats->threshold = p.T;
         if (h.head.err != 0)
             return fail((pr_status)h.head.err, "pr_assign: device reported %s",
+                        pr_status_string((pr_status)h.head.err));
+    }
+    return PR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pr_assign_noalloc: the pr_assign solve for callers that cannot allocate
+// device memory.  Its scratch is one file-scope device array of fixed size.
+// ---------------------------------------------------------------------------
+namespace prot {
+namespace {
+
+constexpr int kNoAllocMaxN = 1024;  // largest n_cols (and so n_rows) accepted
+
+// Bytes the scratch layout below needs for n_rows = n_cols = kNoAllocMaxN,
+// rounded up; checked against the real layout on every call.
+constexpr size_t kNoAllocBytes = (size_t)2304 * 1024;
+
+// Shared by every call on a device and kept until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocLayout {
+    size_t ctl, cb, ka, prop, won, pool, lists, total;
+    int ldq, won_words;
+};
+
+// The regions k_init .. k_finish use.  The per-CTA proposal-list overflow is
+// absent: with n_rows <= 1024 every list fits the shared-memory part.
+NoAllocLayout make_noalloc_layout(int nB, int nA) {
+    NoAllocLayout L;
+    Carver c;
+    L.ldq = (nA + 7) & ~7;
+    L.ctl = c.take<Ctl>(1);
+    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
+    L.ka = c.take<uint16_t>(L.ldq);
+    L.prop = c.take<unsigned long long>((size_t)nA);
+    L.won_words = (nA + 31) / 32;
+    L.won = c.take<unsigned>(3 * (size_t)L.won_words);
+    L.pool = c.take<int2>(2 * (size_t)nB);
+    L.lists = c.take<int>(2 * (size_t)nB);  // completion scratch
+    L.total = c.total();
+    return L;
+}
+
+// Device address of the scratch array for the current device, looked up once
+// per device (cudaGetSymbolAddress must run with that device current).
+pr_status noalloc_scratch(char **out) {
+    static char *addr[64];
+    static bool ready[64];
+    static std::mutex mu;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PR_ERR_INVALID, "pr_assign_noalloc: device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        addr[dev] = (char *)p;
+        ready[dev] = true;
+    }
+    *out = addr[dev];
+    return PR_OK;
+}
+
+}  // namespace
+}  // namespace prot
+
+extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                                       int32_t n_cols, double eps, int32_t *row_to_col,
+                                       int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
+                                       double *cost, pr_stats *stats, void *stream) {
+    if (!C || !row_to_col || !col_to_row || !y_row || !y_col || !cost)
+        return fail(PR_ERR_INVALID, "pr_assign_noalloc: NULL pointer argument");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_noalloc: bad dtype");
+    if (n_rows < 1 || n_cols < n_rows)
+        return fail(PR_ERR_INVALID, "pr_assign_noalloc: need 1 <= n_rows <= n_cols");
+    if (n_cols > kNoAllocMaxN)
+        return fail(PR_ERR_INVALID,
+                    "pr_assign_noalloc: n_cols = %d exceeds the built-in scratch limit of %d "
+                    "(use pr_assign with a caller workspace)",
+                    n_cols, kNoAllocMaxN);
+    if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_noalloc: ldc < n_cols");
+    if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
+        return fail(PR_ERR_INVALID, "pr_assign_noalloc: need 0 < eps < 1 and floor(1/eps) <= 32766");
+    const NoAllocLayout L = make_noalloc_layout(n_rows, n_cols);
+    if (L.total > kNoAllocBytes) return fail(PR_ERR_WORKSPACE, "pr_assign_noalloc: scratch layout too large");
+    PhaseCfg cfg;
+    pr_status rc = phase_cfg(cfg);
+    if (rc != PR_OK) return rc;
+    char *w = nullptr;
+    rc = noalloc_scratch(&w);
+    if (rc != PR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    Params p;
+    p.ctl = (Ctl *)(w + L.ctl);
+    p.cb = (const uint16_t *)(w + L.cb);
+    p.ka = (uint16_t *)(w + L.ka);
+    p.y_b = y_row;
+    p.prop = (unsigned long long *)(w + L.prop);
+    p.won = (unsigned *)(w + L.won);
+    p.won_words = L.won_words;
+    p.pool = (int2 *)(w + L.pool);
+    p.lists = (int *)(w + L.lists);
+    p.list_stride = 0;  // no overflow region: never addressed for n_rows <= 1024
+    p.nB = n_rows;
+    p.nA = n_cols;
+    p.ldq = L.ldq;
+    p.T = (int)floor(eps * (double)n_rows);
+    const long long K = (long long)floor(1.0 / eps);
+    p.phase_cap = ((long long)n_rows * (2 * K + 3)) / (p.T + 1) + 1;
+    p.spin_limit = spin_limit_cycles();
+    p.profile = 0;
+
+    const DeviceInfo &di = device_info();
+    k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
+    PR_CUDA(cudaGetLastError());
+    const long long groups = (long long)n_rows * (L.ldq >> 3);
+    const long long want = groups / 256 + 1;
+    const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
+    const float inv_eps = (float)(1.0 / eps);
+    if (dt == PR_F64)
+        k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps,
+                                                  inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+    else
+        k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps,
+                                                 inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+    PR_CUDA(cudaGetLastError());
+    const int chunks = (L.ldq + kChunk - 1) / kChunk;
+    int warps_per_row = chunks < kWarps ? chunks : kWarps;
+    int rows_per_group = kWarps / warps_per_row;
+    {
+        Params pc = p;
+        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
+        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(cfg.grid), dim3(kThreads),
+                                            args, smem_bytes(L.ldq), st));
+    }
+    k_decode<<<di.sms * 2, 256, 0, st>>>(p, row_to_col, col_to_row, y_col);
+    PR_CUDA(cudaGetLastError());
+    int *free_b = p.lists;
+    int *free_a = p.lists + n_rows;
+    if (dt == PR_F64)
+        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
+                                                    free_b, free_a, cost);
+    else
+        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
+                                                   free_b, free_a, cost);
+    PR_CUDA(cudaGetLastError());
+    if (stats) {
+        Ctl h;
+        PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        stats->phases = h.phases;
+        stats->rounds = h.rounds;
+        stats->bytes_scanned = (int64_t)h.bytes;
+        stats->rows_scanned = (int64_t)h.rows;
+        stats->free_at_stop = h.free_at_stop;
+        stats->threshold = p.T;
+        if (h.head.err != 0)
+            return fail((pr_status)h.head.err, "pr_assign_noalloc: device reported %s",
                         pr_status_string((pr_status)h.head.err));
     }
     return PR_OK;
