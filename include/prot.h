@@ -159,6 +159,23 @@ pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim
                                    const pr_batched_tune *tune, pr_stats *stats, void *ws,
                                    size_t ws_bytes, void *stream);
 
+/*
+ * pr_assign_batched_autotune -- picks the batched solver's launch shape for a
+ * given batch: runs the solve once per candidate (threads per CTA in {128,
+ * 256, 512, 1024} x resident CTAs per SM in {1, 2, 3, 4}; shapes that do not
+ * fit are skipped), times each with CUDA events on `stream`, writes the
+ * fastest to *best (host) and its time in ms to *best_ms (host), and leaves
+ * that shape's results in the outputs.  Points source when XA and XB are both
+ * non-NULL (then C and dt are ignored), otherwise the packed matrices C.  Other
+ * arguments as pr_assign_batched_points / pr_assign_batched.  Synchronous.
+ */
+pr_status pr_assign_batched_autotune(const float *XA, const float *XB, int32_t dim, pr_metric metric,
+                                     const void *C, pr_dtype dt, int32_t n_problems,
+                                     const int32_t *n_host, double eps, int32_t *row_to_col,
+                                     int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
+                                     double *costs, int64_t *phases, pr_batched_tune *best,
+                                     float *best_ms, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Optimal transport (Sec. 4).                                               */
 /* ------------------------------------------------------------------------ */

@@ -113,6 +113,64 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
     return res
 
 
+def _tune_cache_path():
+    import os
+    return os.environ.get("PROT_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "prot", "batched_tune.json"))
+
+
+def _tune_key(torch, dev, kind, sizes, eps, extra=""):
+    import numpy as np
+    n = np.asarray(sizes, dtype=np.int64)
+    name = torch.cuda.get_device_name(dev)
+    return f"{name}|{kind}{extra}|P={n.size}|nmax={int(n.max())}|n2={int((n * n).sum())}|eps={eps!r}"
+
+
+def _tune_lookup(key):
+    import json
+    try:
+        with open(_tune_cache_path()) as f:
+            v = json.load(f).get(key)
+        return (int(v[0]), int(v[1])) if v else None
+    except (OSError, ValueError):
+        return None
+
+
+def _tune_store(key, tune):
+    import json
+    import os
+    path = _tune_cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        try:
+            with open(path) as f:
+                d = json.load(f)
+        except (OSError, ValueError):
+            d = {}
+        d[key] = [int(tune[0]), int(tune[1])]
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home: the choice is simply not remembered
+
+
+def _autotune(torch, L, dev, kind, args_src, sizes, n_ptr, eps, out, wsb):
+    """Run the library's autotuner for this batch; returns (threads, ctas_per_sm)."""
+    best = _lib.PrBatchedTune()
+    ms = ctypes.c_float()
+    XA, XB, dim, metric, C, dt = args_src
+    rc = L.pr_assign_batched_autotune(XA, XB, dim, metric, C, dt, len(sizes), n_ptr, float(eps),
+                                      out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
+                                      out["y_row"].data_ptr(), out["y_col"].data_ptr(),
+                                      out["costs"].data_ptr(), out["phases"].data_ptr(),
+                                      ctypes.byref(best), ctypes.byref(ms), wsb.data_ptr(), wsb.numel(),
+                                      _stream_handle(torch, dev))
+    _lib.check(rc, "pr_assign_batched_autotune")
+    return (best.threads, best.ctas_per_sm)
+
+
 def _tune_struct(tune):
     if tune is None:
         return None
@@ -168,6 +226,13 @@ def assign_batched(C, sizes, eps: float, *, tune=None, sync: bool = True,
         raise PrError(_lib.PR_ERR_INVALID, "invalid problem sizes (need 1 <= n_i <= 5000)")
     wsb = (ws or _workspace(dev)).get(need)
     out = out or _batched_outputs(torch, dev, n)
+    if isinstance(tune, str):
+        key = _tune_key(torch, dev, "matrix", n, eps, extra=str(C.dtype))
+        tune = _tune_lookup(key)
+        if tune is None:
+            tune = _autotune(torch, L, dev, "matrix", (None, None, 0, 0, C.data_ptr(), dt), n, n_ptr, eps,
+                             out, wsb)
+            _tune_store(key, tune)
     st = _lib.PrStats()
     rc = L.pr_assign_batched(C.data_ptr(), dt, len(n), n_ptr, float(eps),
                              out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
@@ -210,6 +275,13 @@ def assign_batched_points(XA, XB, sizes, eps: float, *, metric: str = "sqeuclide
         raise PrError(_lib.PR_ERR_INVALID, "invalid problem sizes (need 1 <= n_i <= 5000)")
     wsb = (ws or _workspace(dev)).get(need)
     out = out or _batched_outputs(torch, dev, n)
+    if isinstance(tune, str):
+        key = _tune_key(torch, dev, "points", n, eps, extra=f"{metric}d{XA.shape[1]}")
+        tune = _tune_lookup(key)
+        if tune is None:
+            tune = _autotune(torch, L, dev, "points", (XA.data_ptr(), XB.data_ptr(), XA.shape[1], m, None, 0),
+                             n, n_ptr, eps, out, wsb)
+            _tune_store(key, tune)
     st = _lib.PrStats()
     rc = L.pr_assign_batched_points(XA.data_ptr(), XB.data_ptr(), XA.shape[1], m, len(n), n_ptr,
                                     float(eps), out["row_to_col"].data_ptr(),
@@ -262,7 +334,7 @@ def _assign_loss_function():
             B, n, d = X.shape
             sizes = [n] * B
             res = assign_batched_points(Y.detach().reshape(B * n, d), X.detach().reshape(B * n, d),
-                                        sizes, eps, metric="sqeuclidean", sync=False)
+                                        sizes, eps, metric="sqeuclidean", sync=False, tune="auto")
             ctx.save_for_backward(X, Y, res["row_to_col"])
             ctx.plan = res
             return (res["costs"] / n).to(X.dtype)

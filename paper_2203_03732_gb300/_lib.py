@@ -79,6 +79,10 @@ SIGNATURES = {
     "pr_assign_backward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "pr_assign_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                          _vp, ctypes.POINTER(PrStats), _vp]),
+    "pr_assign_batched_autotune": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _vp, ctypes.c_int, _i32, _vp,
+                                                  _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                  ctypes.POINTER(PrBatchedTune), ctypes.POINTER(ctypes.c_float),
+                                                  _vp, _sz, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),
     "pr_set_kernel_events": (None, [_vp, _vp]),
     "pr_last_error": (ctypes.c_char_p, []),

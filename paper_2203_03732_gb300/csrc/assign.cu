@@ -752,13 +752,12 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     const long long groups = (long long)n_rows * (L.ldq >> 3);
     const long long want = groups / 256 + 1;
     const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
-    const float inv_eps = (float)(1.0 / eps);
     if (dt == PR_F64)
-        k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                  inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+        launch_quantise<double>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
+                                &p.ctl->head, qgrid, st);
     else
-        k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                 inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+        launch_quantise<float>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
+                               &p.ctl->head, qgrid, st);
     PR_CUDA(cudaGetLastError());
 
     const int chunks = (L.ldq + kChunk - 1) / kChunk;
@@ -921,13 +920,12 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
     const long long groups = (long long)n_rows * (L.ldq >> 3);
     const long long want = groups / 256 + 1;
     const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
-    const float inv_eps = (float)(1.0 / eps);
     if (dt == PR_F64)
-        k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                  inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+        launch_quantise<double>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
+                                &p.ctl->head, qgrid, st);
     else
-        k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps,
-                                                 inv_eps, (uint16_t *)p.cb, &p.ctl->head);
+        launch_quantise<float>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
+                               &p.ctl->head, qgrid, st);
     PR_CUDA(cudaGetLastError());
     const int chunks = (L.ldq + kChunk - 1) / kChunk;
     int warps_per_row = chunks < kWarps ? chunks : kWarps;

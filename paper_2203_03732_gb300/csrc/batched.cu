@@ -23,6 +23,7 @@
 
 #include "prot_internal.cuh"
 #include "scan_common.cuh"
+#include "quantise.cuh"
 
 namespace prot {
 namespace {
@@ -124,12 +125,10 @@ __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict
             for (int k = 0; k < 2; ++k) {
                 const int a = a0 + 2 * j + k;
                 if (a < D.n) {
-                    const double c = (double)row[a];
-                    if (!(c >= 0.0 && c <= 1.0)) {
+                    h[k] = quantise_elem(row, a, eps, inv_eps);
+                    if (h[k] == 0xFFFFFFFFu) {
                         bad = true;
                         h[k] = 0;
-                    } else {
-                        h[k] = quantise_one(c, eps, inv_eps);
                     }
                 } else {
                     h[k] = kPadCost;
@@ -213,7 +212,7 @@ __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__res
             if (a < D.n) {
                 const float dd = dist_f32(xb, XA + (long long)(D.v_off + a) * dim, dim, squared);
                 const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
-                h[j] = quantise_one((double)c, eps, inv_eps);
+                h[j] = quantise_fbits(__float_as_uint(c), eps, inv_eps);
             } else {
                 h[j] = kPadCost;
             }
@@ -236,17 +235,19 @@ struct BShared {
 };
 
 // Lowest column a >= start of the row with cbar + k(a) == tgt whose word does
-// not carry a tag in [Rps, R) (taken earlier in this phase), or -1.
+// not carry a tag in [Rps, R) (taken earlier in this phase), or -1.  UNROLL
+// 16-byte loads per lane are in flight per step.
+template <int UNROLL>
 __device__ __forceinline__ int warp_scan_row(const uint16_t *__restrict__ row, const uint16_t *ks,
                                              const unsigned long long *pw, int start, int ldq,
                                              uint32_t tgt, unsigned R, unsigned Rps, int lane,
                                              unsigned long long &bytes) {
     const uint32_t t2 = tgt | (tgt << 16);
     const bool check_taken = R > Rps;
-    for (int c0 = start & ~7; c0 < ldq; c0 += kChunk) {
-        uint4 sv[kUnroll];
+    for (int c0 = start & ~7; c0 < ldq; c0 += 256 * UNROLL) {
+        uint4 sv[UNROLL];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < UNROLL; ++u) {
             const int idx = c0 + u * 256 + lane * 8;
             if (idx < ldq) {
                 const uint4 c = ld_nc_na_v4(row + idx);
@@ -256,9 +257,9 @@ __device__ __forceinline__ int warp_scan_row(const uint16_t *__restrict__ row, c
                 sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
             }
         }
-        bytes += 2ull * (unsigned long long)min(kChunk, ldq - c0);
+        bytes += 2ull * (unsigned long long)min(256 * UNROLL, ldq - c0);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < UNROLL; ++u) {
             const int idx = c0 + u * 256 + lane * 8;
             unsigned m = eq_mask(sv[u], t2);
             const int lo = start - idx;
@@ -304,8 +305,8 @@ __device__ __forceinline__ int block_scan_excl(int flag, BShared &s) {
     return r;
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_bsolve(BParams p) {
+template <int THREADS, int UNROLL>
+__global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ BShared s;
     // region sizes use n_max rounded up to a multiple of 8, so every region
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(THREADS) k_bsolve(BParams p) {
                         start = q.y + 1;                     // lost: resume after a
                     }
                     const uint32_t tgt = (uint32_t)(yb[b] - 1);
-                    const int a = warp_scan_row(cb + (long long)b * ldq, ks, pw, start, ldq, tgt, R,
+                    const int a = warp_scan_row<UNROLL>(cb + (long long)b * ldq, ks, pw, start, ldq, tgt, R,
                                                 Rps, lane, my_bytes);
                     if (lane == 0) {
                         if (a >= 0) {
@@ -652,10 +653,10 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     const size_t smem = bsolve_smem(pl.n_max, pl.ldq_max, threads);
     if (smem > (size_t)di.max_smem_optin)
         return fail(PR_ERR_INVALID, "batched: problem of n = %d does not fit shared memory", pl.n_max);
-    const void *kern = threads == 128   ? (const void *)k_bsolve<128>
-                       : threads == 256 ? (const void *)k_bsolve<256>
-                       : threads == 512 ? (const void *)k_bsolve<512>
-                                        : (const void *)k_bsolve<1024>;
+    const void *kern = threads == 128   ? (const void *)k_bsolve<128, 8>
+                       : threads == 256 ? (const void *)k_bsolve<256, 8>
+                       : threads == 512 ? (const void *)k_bsolve<512, 8>
+                                        : (const void *)k_bsolve<1024, 4>;
     PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -756,4 +757,75 @@ extern "C" pr_status pr_assign_batched_points(const float *XA, const float *XB, 
     src.points = true;
     return run_batched(src, n_problems, n_host, eps, row_to_col, col_to_row, y_row, y_col, costs,
                        phases, tune, stats, ws, ws_bytes, stream);
+}
+
+// Launch-shape autotuner for the batched solver: runs the solve once with
+// every candidate (threads per CTA x resident CTAs per SM) on the caller's
+// batch, times each with CUDA events on `stream`, and returns the fastest.
+// The outputs hold the last candidate's (identical) results.
+extern "C" pr_status pr_assign_batched_autotune(const float *XA, const float *XB, int32_t dim,
+                                                pr_metric metric, const void *C, pr_dtype dt,
+                                                int32_t n_problems, const int32_t *n_host, double eps,
+                                                int32_t *row_to_col, int32_t *col_to_row,
+                                                int32_t *y_row, int32_t *y_col, double *costs,
+                                                int64_t *phases, pr_batched_tune *best,
+                                                float *best_ms, void *ws, size_t ws_bytes,
+                                                void *stream) {
+    if (!best || !best_ms) return fail(PR_ERR_INVALID, "pr_assign_batched_autotune: NULL result pointer");
+    const bool points = XA && XB;
+    if (!points && !C) return fail(PR_ERR_INVALID, "pr_assign_batched_autotune: give points or costs");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto run = [&](const pr_batched_tune *t) -> pr_status {
+        return points ? pr_assign_batched_points(XA, XB, dim, metric, n_problems, n_host, eps, row_to_col,
+                                                 col_to_row, y_row, y_col, costs, phases, t, nullptr, ws,
+                                                 ws_bytes, stream)
+                      : pr_assign_batched(C, dt, n_problems, n_host, eps, row_to_col, col_to_row, y_row,
+                                          y_col, costs, phases, t, nullptr, ws, ws_bytes, stream);
+    };
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    const int threads_c[] = {128, 256, 512, 1024};
+    const int per_sm_c[] = {1, 2, 3, 4};
+    float best_t = -1.0f;
+    pr_batched_tune bt{0, 0};
+    bool warmed = false;
+    pr_status last_err = PR_OK;
+    for (int th : threads_c) {
+        for (int ps : per_sm_c) {
+            pr_batched_tune t{th, ps};
+            if (!warmed) {
+                if (run(&t) != PR_OK) {
+                    last_err = PR_ERR_INVALID;
+                    continue;
+                }
+                warmed = true;
+            }
+            cudaEventRecord(e0, st);
+            const pr_status rc = run(&t);
+            cudaEventRecord(e1, st);
+            if (rc != PR_OK) {  // this shape does not fit: skip it
+                last_err = rc;
+                cudaStreamSynchronize(st);
+                continue;
+            }
+            PR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (best_t < 0.0f || ms < best_t) {
+                best_t = ms;
+                bt = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_t < 0.0f) return fail(last_err != PR_OK ? last_err : PR_ERR_INVALID,
+                                   "pr_assign_batched_autotune: no launch shape worked");
+    // the solve with the chosen shape leaves its results in the outputs
+    const pr_status rc = run(&bt);
+    if (rc != PR_OK) return rc;
+    *best = bt;
+    *best_ms = best_t;
+    return PR_OK;
 }

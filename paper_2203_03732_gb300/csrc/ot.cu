@@ -708,13 +708,12 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         const long long groups = (long long)nB * (L.ldq >> 3);
         const long long want = groups / 256 + 1;
         const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
-        const float inv_eps = (float)(1.0 / eps);
         if (dt == PR_F64)
-            k_quantise<double><<<qgrid, 256, 0, st>>>((const double *)C, ldc, nB, nA, L.ldq, eps, inv_eps,
-                                                      (uint16_t *)p.cb, &p.ctl->head);
+            launch_quantise<double>((const double *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)p.cb,
+                                    &p.ctl->head, qgrid, st);
         else
-            k_quantise<float><<<qgrid, 256, 0, st>>>((const float *)C, ldc, nB, nA, L.ldq, eps, inv_eps,
-                                                     (uint16_t *)p.cb, &p.ctl->head);
+            launch_quantise<float>((const float *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)p.cb,
+                                   &p.ctl->head, qgrid, st);
         PR_CUDA(cudaGetLastError());
     }
     OCtl h;

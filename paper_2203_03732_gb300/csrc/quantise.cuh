@@ -9,9 +9,18 @@ namespace prot {
 namespace {
 
 // ---------------------------------------------------------------------------
-// k_quantise: Eq. (1) exactly (quantise_one), 8 columns per thread.
+// k_quantise: Eq. (1) exactly, 8 columns per thread, one 16-byte store.  With
+// VEC the row's 8 costs are read with 16-byte loads (rows 16-byte aligned).
 // ---------------------------------------------------------------------------
-template <class T>
+__device__ __forceinline__ uint32_t quantise_elem(const double *row, int a, double eps, float inv_eps) {
+    const unsigned long long bits = __double_as_longlong(row[a]);
+    return quantise_bits((uint32_t)(bits >> 32), (uint32_t)bits, eps, inv_eps);
+}
+__device__ __forceinline__ uint32_t quantise_elem(const float *row, int a, double eps, float inv_eps) {
+    return quantise_fbits(__float_as_uint(row[a]), eps, inv_eps);
+}
+
+template <class T, bool VEC>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
                            double eps, float inv_eps, uint16_t *__restrict__ cb, WsHead *head) {
     const int groups = ldq >> 3;
@@ -22,30 +31,54 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
         const int b = (int)(g / groups);
         const int a0 = (int)(g - (long long)b * groups) << 3;
         const T *row = C + (long long)b * ldc;
-        uint32_t w[4];
+        uint32_t h[8];
+        if (VEC && a0 + 8 <= nA) {
+            // 8 consecutive costs: 4 x 16 B (FP64) or 2 x 16 B (FP32)
+            if (sizeof(T) == 8) {
+                const uint4 *v = reinterpret_cast<const uint4 *>(row + a0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t h[2];
+                for (int j = 0; j < 4; ++j) {
+                    const uint4 x = __ldg(v + j);
+                    h[2 * j] = quantise_bits(x.y, x.x, eps, inv_eps);
+                    h[2 * j + 1] = quantise_bits(x.w, x.z, eps, inv_eps);
+                }
+            } else {
+                const uint4 *v = reinterpret_cast<const uint4 *>(row + a0);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int a = a0 + 2 * j + k;
-                if (a < nA) {
-                    const double c = (double)row[a];
-                    if (!(c >= 0.0 && c <= 1.0)) {
-                        bad = true;
-                        h[k] = 0;
-                    } else {
-                        h[k] = quantise_one(c, eps, inv_eps);
-                    }
-                } else {
-                    h[k] = kPadCost;
+                for (int j = 0; j < 2; ++j) {
+                    const uint4 x = __ldg(v + j);
+                    h[4 * j] = quantise_fbits(x.x, eps, inv_eps);
+                    h[4 * j + 1] = quantise_fbits(x.y, eps, inv_eps);
+                    h[4 * j + 2] = quantise_fbits(x.z, eps, inv_eps);
+                    h[4 * j + 3] = quantise_fbits(x.w, eps, inv_eps);
                 }
             }
-            w[j] = h[0] | (h[1] << 16);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                h[j] = a0 + j < nA ? quantise_elem(row, a0 + j, eps, inv_eps) : (uint32_t)kPadCost;
         }
-        *reinterpret_cast<uint4 *>(cb + (long long)b * ldq + a0) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (h[j] == 0xFFFFFFFFu) {
+                bad = true;
+                h[j] = 0;
+            }
+        }
+        *reinterpret_cast<uint4 *>(cb + (long long)b * ldq + a0) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
     }
     if (bad) record_error(head, PR_ERR_INVALID);
+}
+
+// Launch k_quantise with 16-byte loads when every row starts 16-byte aligned.
+template <class T>
+void launch_quantise(const T *C, long long ldc, int nB, int nA, int ldq, double eps, uint16_t *cb,
+                     WsHead *head, int grid, cudaStream_t st) {
+    const float inv_eps = (float)(1.0 / eps);
+    const bool vec = ((uintptr_t)C % 16 == 0) && ((ldc * (long long)sizeof(T)) % 16 == 0);
+    if (vec) k_quantise<T, true><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, eps, inv_eps, cb, head);
+    else k_quantise<T, false><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, eps, inv_eps, cb, head);
 }
 
 }  // namespace

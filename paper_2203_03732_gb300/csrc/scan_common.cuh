@@ -12,18 +12,53 @@ namespace prot {
 constexpr uint16_t kPadCost = 0x7FFF;  // cbar of padding columns
 constexpr uint16_t kPadKey = 0x8000;   // k of padding columns: pad sum 0xFFFF never matches
 
-// Eq. (1) exactly: the largest k with k * eps <= c, for 0 <= c <= 1.
-// An FP32 estimate q of c/eps is within 0.006 of the exact quotient (three
-// roundings of relative size 2^-24 on a quotient <= 32767), so floor(q) is
-// exact whenever q is at least 1/64 away from an integer.  Otherwise the
-// integer is settled with fma(-k, eps, c), whose sign is that of the exact
-// c - k*eps.  No FP64 division runs per element.
-__device__ __forceinline__ uint32_t quantise_one(double c, double eps, float inv_eps) {
-    const float q = __fmul_rn((float)c, inv_eps);
+// Eq. (1) exactly: cbar = the largest k with k * eps <= c, for 0 <= c <= 1.
+// An FP32 estimate q of c/eps is within 0.008 of the exact quotient (see
+// below), so floor(q) is exact whenever q is at least 1/64 away from an
+// integer.  Otherwise the integer is settled with fma(-k, eps, c), whose sign
+// is that of the exact c - k*eps.  No FP64 division runs per element.
+//
+// For an FP64 cost given by its bit pattern, with no FP64
+// instruction on the common path (GB300 runs FP64 at a small fraction of its
+// FP32 rate).  Range test on the bits: 0 <= c <= 1 (or -0.0), which also
+// rejects NaN and infinities.  The FP32 estimate truncates the mantissa
+// (relative error < 2^-23) before the two roundings of the product, so q is
+// within 0.008 of the exact quotient and the 1/64 margin still holds.
+// Returns 0xFFFFFFFF for a cost outside [0, 1].
+__device__ __forceinline__ uint32_t quantise_bits(uint32_t hi, uint32_t lo, double eps, float inv_eps) {
+    if (hi >= 0x80000000u) {  // sign bit: only -0.0 is valid
+        return (hi == 0x80000000u && lo == 0u) ? 0u : 0xFFFFFFFFu;
+    }
+    if (hi > 0x3FF00000u || (hi == 0x3FF00000u && lo != 0u)) return 0xFFFFFFFFu;  // > 1, NaN, inf
+    const uint32_t e = hi >> 20;
+    if (e <= 896u) {
+        // c < 2^-126 (zero or tiny): floor(c / eps) is 0 unless eps is tinier,
+        // which eps >= 1/32767 rules out
+        return 0u;
+    }
+    const uint32_t fbits = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const float q = __fmul_rn(__uint_as_float(fbits), inv_eps);
     const float kf = floorf(q);
     const float fr = q - kf;
     int k = (int)kf;
     if (!(fr >= 0.015625f && fr <= 0.984375f)) {
+        const double c = __hiloint2double((int)hi, (int)lo);
+        while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
+        while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
+    }
+    return (uint32_t)k;
+}
+
+// The same for an FP32 cost: range test on the bits, exact FP32 estimate.
+__device__ __forceinline__ uint32_t quantise_fbits(uint32_t fb, double eps, float inv_eps) {
+    if (fb >= 0x80000000u) return fb == 0x80000000u ? 0u : 0xFFFFFFFFu;
+    if (fb > 0x3F800000u) return 0xFFFFFFFFu;
+    const float q = __fmul_rn(__uint_as_float(fb), inv_eps);
+    const float kf = floorf(q);
+    const float fr = q - kf;
+    int k = (int)kf;
+    if (!(fr >= 0.015625f && fr <= 0.984375f)) {
+        const double c = (double)__uint_as_float(fb);
         while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
         while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
     }

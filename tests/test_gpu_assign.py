@@ -207,3 +207,21 @@ def test_async_status_query(prot):
     assert rc == 0
     ref = oracle.assign(C, 0.1)
     assert np.array_equal(r["row_to_col"].cpu().numpy(), ref["row_to_col"])
+
+
+@pytest.mark.parametrize("eps,dtype", [(0.1, np.float64), (0.01, np.float64), (1.0 / 3.0, np.float64),
+                                       (0.005, np.float32), (1.0 / 32766.5, np.float64)])
+def test_rounding_on_and_next_to_multiples_of_eps(prot, eps, dtype):
+    """Costs on multiples of eps and one ulp either side, plus 0, -0.0, 1 and
+    denormals: Eq. (1)'s exact floor decides every one of them, so any
+    rounding slip changes the duals."""
+    g = np.random.default_rng(3)
+    n = 384
+    K = int(np.floor(1.0 / eps))
+    k = g.integers(0, K + 1, size=(n, n)).astype(dtype)
+    base = (k * dtype(eps)).astype(dtype)
+    side = g.integers(-1, 2, size=(n, n))
+    C = np.where(side < 0, np.nextafter(base, dtype(0)), np.where(side > 0, np.nextafter(base, dtype(2)), base))
+    C = np.clip(C, 0, 1).astype(dtype)
+    C[0, :4] = [0.0, -0.0, 1.0, np.finfo(dtype).tiny / 4]
+    assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))

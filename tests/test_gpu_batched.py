@@ -135,3 +135,27 @@ def test_batched_bad_sizes(prot):
     with pytest.raises((prot.PrError, ValueError)):
         prot.assign_batched(torch.zeros(36000000, dtype=torch.float64, device="cuda"),
                             np.array([6000], np.int32), 0.1)
+
+
+def test_autotune_picks_a_shape_and_keeps_results(prot, tmp_path, monkeypatch):
+    """The library's autotuner times every launch shape on the batch; the
+    chosen shape is cached, and the results equal the oracle's."""
+    import json
+    import torch
+    monkeypatch.setenv("PROT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    sizes = W.batched_sizes(40, 64, 900, seed=12)
+    XA, XB, off = W.batched_points_3d(sizes, seed=12)
+    XAd, XBd = torch.from_numpy(XA).cuda(), torch.from_numpy(XB).cuda()
+    got = prot.assign_batched_points(XAd, XBd, sizes, 0.01, tune="auto")
+    cache = json.load(open(tmp_path / "tune.json"))
+    assert len(cache) == 1
+    threads, per_sm = next(iter(cache.values()))
+    assert threads in (128, 256, 512, 1024) and 1 <= per_sm <= 4
+    got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in got.items()}
+    for i in (0, 7, 39):
+        s, e = off[i], off[i + 1]
+        ref = OP.assign_points(XA[s:e], XB[s:e], 0.01, squared=True)
+        check_problem(got, i, int(s), int(sizes[i]), ref)
+    # a second call reads the cache and gives the same result
+    again = prot.assign_batched_points(XAd, XBd, sizes, 0.01, tune="auto")
+    assert np.array_equal(again["row_to_col"].cpu().numpy(), got["row_to_col"])
