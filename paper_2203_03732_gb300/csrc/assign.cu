@@ -65,12 +65,17 @@ struct Ctl {
     long long rounds;
     unsigned long long bytes;
     unsigned long long rows;
-    // PR_PROFILE=1: CTA 0's %globaltimer split of the rounds (ns): round
-    // start (bitmaps, keys), items + scans + proposals, barrier; round count;
-    // summed over rounds: the slowest CTA's work time and largest item count.
-    unsigned long long prof[6];
-    unsigned long long prof_slot[2][2];  // per round parity: max work ns, max items
+    // PR_PROFILE=1: a %globaltimer split of every round (ns) into kProfSegs
+    // segments: round start (bitmaps, keys), item build, row scans,
+    // proposals, donations and the rest, grid barrier; then the item count.
+    // prof_own sums CTA 0's values over the rounds, prof_max sums the
+    // per-round maximum over CTAs of each segment; prof_rounds counts rounds.
+    unsigned long long prof_own[8];
+    unsigned long long prof_max[8];
+    unsigned long long prof_slot[2][8];  // per round parity: max over CTAs
+    unsigned long long prof_rounds;
 };
+constexpr int kProfSegs = 7;
 
 struct Layout {
     size_t ctl, cb, ka, prop, won, pool, lists, total;
@@ -199,6 +204,7 @@ struct Smem {
     unsigned long long bytes;
     unsigned long long rows;
     unsigned long long pub, pub2;
+    unsigned long long pacc[4];  // profile: build, scan, proposal, tail ns of this round
     int err;
 };
 
@@ -282,6 +288,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                                          int rows_per_group) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
+    const unsigned long long tA = p.profile ? gtimer() : 0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x)
         if (s.job_tgt[j] < 0) s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
@@ -313,6 +320,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (threadIdx.x < ng) s.job_best[g0 + threadIdx.x] = s.best[threadIdx.x];
     }
     __syncthreads();
+    const unsigned long long tB = p.profile ? gtimer() : 0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
         const int b = s.job_b[j];
         const int a = s.job_best[j];
@@ -342,6 +350,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         }
     }
     __syncthreads();
+    const unsigned long long tC = p.profile ? gtimer() : 0;
     if (s.ndon > 0) {
         if (threadIdx.x == 0) s.don_base = atomicAdd(pool_cnt, s.ndon);
         __syncthreads();
@@ -355,6 +364,11 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
     if (threadIdx.x == 0) {
         s.rows += (unsigned long long)nq;
         s.njob = 0;
+        if (p.profile) {
+            s.pacc[1] += tB - tA;
+            s.pacc[2] += tC - tB;
+            s.pacc[3] += gtimer() - tC;
+        }
     }
     __syncthreads();
 }
@@ -419,6 +433,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             const unsigned long long t_r0 = p.profile ? gtimer() : 0;
             unsigned *won_now = p.won + (size_t)(R % 3) * p.won_words;
             if (threadIdx.x == 0) {
+                s.pacc[0] = s.pacc[1] = s.pacc[2] = s.pacc[3] = 0;
                 s.had_prop = 0;
                 s.nonfirst = 0;
                 s.nf_delta = 0;
@@ -468,6 +483,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             }
             __syncthreads();
             const unsigned long long t_r1 = p.profile ? gtimer() : 0;
+            unsigned long long t_mark = t_r1;
             for (int i0 = 0; i0 < nitems; i0 += kBatch) {
                 const int cnt = min(kBatch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -501,31 +517,43 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     s.job_tgt[j] = y >= 0 ? y - 1 : -1;
                 }
                 __syncthreads();
+                if (p.profile && threadIdx.x == 0) s.pacc[0] += gtimer() - t_mark;
                 run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
                          &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group);
+                if (p.profile) t_mark = gtimer();
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
                                             ((unsigned long long)s.nonfirst << 20) |
                                             ((unsigned long long)s.nf_delta << 40);
             const unsigned long long t_r2 = p.profile ? gtimer() : 0;
+            unsigned long long seg[kProfSegs] = {};
             if (p.profile && threadIdx.x == 0) {
-                atomicMax(&ctl->prof_slot[R & 1][0], t_r2 - t_r1);
-                atomicMax(&ctl->prof_slot[R & 1][1], (unsigned long long)nitems);
+                seg[0] = t_r1 - t_r0;
+                seg[1] = s.pacc[0];
+                seg[2] = s.pacc[1];
+                seg[3] = s.pacc[2];
+                seg[4] = s.pacc[3] + (t_r2 - t_mark);
+                seg[6] = (unsigned long long)nitems;
+                for (int k = 0; k < kProfSegs; ++k)
+                    if (k != 5) atomicMax(&ctl->prof_slot[R & 1][k], seg[k]);
                 if (cta == 0) {
-                    // read after round R - 1; written again only after this barrier
-                    ctl->prof_slot[(R + 1) & 1][0] = 0;
-                    ctl->prof_slot[(R + 1) & 1][1] = 0;
+                    // read after round R - 1; written again (the barrier
+                    // segment of round R) only after this barrier
+                    for (int k = 0; k < kProfSegs; ++k) ctl->prof_slot[(R + 1) & 1][k] = 0;
                 }
             }
             if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)) goto done;
-            if (p.profile && cta == 0 && threadIdx.x == 0) {
-                const unsigned long long t_r3 = gtimer();
-                ctl->prof[0] += t_r1 - t_r0;
-                ctl->prof[1] += t_r2 - t_r1;
-                ctl->prof[2] += t_r3 - t_r2;
-                ctl->prof[3] += 1;
-                ctl->prof[4] += ctl->prof_slot[R & 1][0];
-                ctl->prof[5] += ctl->prof_slot[R & 1][1];
+            if (p.profile && threadIdx.x == 0) {
+                seg[5] = gtimer() - t_r2;
+                // the barrier segment of round R goes to the next round's slot
+                atomicMax(&ctl->prof_slot[(R + 1) & 1][5], seg[5]);
+                if (cta == 0) {
+                    for (int k = 0; k < kProfSegs; ++k) {
+                        ctl->prof_own[k] += seg[k];
+                        ctl->prof_max[k] += ctl->prof_slot[R & 1][k];
+                    }
+                    ctl->prof_rounds += 1;
+                }
             }
             const unsigned long long pub = s.pub;
             if ((pub >> 31) & 1ull) ++rounds;

@@ -105,7 +105,7 @@ __device__ __forceinline__ int problem_of(const BDesc *d, int P, long long g) {
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict__ d, int P,
-                                long long total_groups, double eps, float inv_eps,
+                                long long total_groups, EpsSplit e,
                                 uint16_t *__restrict__ cb, WsHead *head) {
     bool bad = false;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
@@ -125,7 +125,7 @@ __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict
             for (int k = 0; k < 2; ++k) {
                 const int a = a0 + 2 * j + k;
                 if (a < D.n) {
-                    h[k] = quantise_elem(row, a, eps, inv_eps);
+                    h[k] = quantise_elem(row, a, e);
                     if (h[k] == 0xFFFFFFFFu) {
                         bad = true;
                         h[k] = 0;
@@ -194,7 +194,7 @@ __global__ void k_bpoints_max(const float *__restrict__ XA, const float *__restr
 __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
                                 int squared, const BDesc *__restrict__ d, int P,
                                 long long total_groups, const unsigned *__restrict__ maxbits,
-                                double eps, float inv_eps, uint16_t *__restrict__ cb) {
+                                EpsSplit e, uint16_t *__restrict__ cb) {
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
          g += (long long)gridDim.x * blockDim.x) {
         const int i = problem_of(d, P, g);
@@ -212,7 +212,7 @@ __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__res
             if (a < D.n) {
                 const float dd = dist_f32(xb, XA + (long long)(D.v_off + a) * dim, dim, squared);
                 const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
-                h[j] = quantise_fbits(__float_as_uint(c), eps, inv_eps);
+                h[j] = quantise_fbits(__float_as_uint(c), e);
             } else {
                 h[j] = kPadCost;
             }
@@ -633,19 +633,19 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     PR_CUDA(cudaMemcpyAsync(d_desc, pl.desc.data(), sizeof(BDesc) * P, cudaMemcpyHostToDevice, st));
     PR_CUDA(cudaMemcpyAsync(d_order, pl.order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
 
-    const float inv_eps = (float)(1.0 / eps);
+    const EpsSplit e = make_eps_split(eps);
     const long long want = pl.groups / 256 + 1;
     const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
     if (src.points) {
         k_bpoints_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups, d_max);
         PR_CUDA(cudaGetLastError());
         k_bpoints_quant<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups,
-                                               d_max, eps, inv_eps, d_cb);
+                                               d_max, e, d_cb);
     } else if (src.dt == PR_F64) {
-        k_bquant_matrix<double><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, eps,
-                                                       inv_eps, d_cb, &ctl->head);
+        k_bquant_matrix<double><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, e,
+                                                       d_cb, &ctl->head);
     } else {
-        k_bquant_matrix<float><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, eps, inv_eps,
+        k_bquant_matrix<float><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
                                                       d_cb, &ctl->head);
     }
     PR_CUDA(cudaGetLastError());

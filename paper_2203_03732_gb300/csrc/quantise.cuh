@@ -12,24 +12,32 @@ namespace {
 // k_quantise: Eq. (1) exactly, 8 columns per thread, one 16-byte store.  With
 // VEC the row's 8 costs are read with 16-byte loads (rows 16-byte aligned).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t quantise_elem(const double *row, int a, double eps, float inv_eps) {
+__device__ __forceinline__ uint32_t quantise_elem(const double *row, int a, const EpsSplit &e) {
     const unsigned long long bits = __double_as_longlong(row[a]);
-    return quantise_bits((uint32_t)(bits >> 32), (uint32_t)bits, eps, inv_eps);
+    return quantise_bits((uint32_t)(bits >> 32), (uint32_t)bits, e);
 }
-__device__ __forceinline__ uint32_t quantise_elem(const float *row, int a, double eps, float inv_eps) {
-    return quantise_fbits(__float_as_uint(row[a]), eps, inv_eps);
+__device__ __forceinline__ uint32_t quantise_elem(const float *row, int a, const EpsSplit &e) {
+    return quantise_fbits(__float_as_uint(row[a]), e);
 }
 
 template <class T, bool VEC>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
-                           double eps, float inv_eps, uint16_t *__restrict__ cb, WsHead *head) {
+                           EpsSplit e, uint16_t *__restrict__ cb, WsHead *head) {
+    // Grid-stride over (row, group of 8 columns); the row and group indices
+    // advance by the stride's quotient and remainder (no division per step).
     const int groups = ldq >> 3;
-    const long long total = (long long)nB * groups;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int step_b = (int)(stride / groups), step_g = (int)(stride % groups);
+    int b = (int)(g0 / groups), gi = (int)(g0 % groups);
     bool bad = false;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(g / groups);
-        const int a0 = (int)(g - (long long)b * groups) << 3;
+    for (; b < nB; b += step_b, gi += step_g) {
+        if (gi >= groups) {
+            gi -= groups;
+            ++b;
+            if (b >= nB) break;
+        }
+        const int a0 = gi << 3;
         const T *row = C + (long long)b * ldc;
         uint32_t h[8];
         if (VEC && a0 + 8 <= nA) {
@@ -39,24 +47,24 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint4 x = __ldg(v + j);
-                    h[2 * j] = quantise_bits(x.y, x.x, eps, inv_eps);
-                    h[2 * j + 1] = quantise_bits(x.w, x.z, eps, inv_eps);
+                    h[2 * j] = quantise_bits(x.y, x.x, e);
+                    h[2 * j + 1] = quantise_bits(x.w, x.z, e);
                 }
             } else {
                 const uint4 *v = reinterpret_cast<const uint4 *>(row + a0);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const uint4 x = __ldg(v + j);
-                    h[4 * j] = quantise_fbits(x.x, eps, inv_eps);
-                    h[4 * j + 1] = quantise_fbits(x.y, eps, inv_eps);
-                    h[4 * j + 2] = quantise_fbits(x.z, eps, inv_eps);
-                    h[4 * j + 3] = quantise_fbits(x.w, eps, inv_eps);
+                    h[4 * j] = quantise_fbits(x.x, e);
+                    h[4 * j + 1] = quantise_fbits(x.y, e);
+                    h[4 * j + 2] = quantise_fbits(x.z, e);
+                    h[4 * j + 3] = quantise_fbits(x.w, e);
                 }
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                h[j] = a0 + j < nA ? quantise_elem(row, a0 + j, eps, inv_eps) : (uint32_t)kPadCost;
+                h[j] = a0 + j < nA ? quantise_elem(row, a0 + j, e) : (uint32_t)kPadCost;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -75,10 +83,10 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
 template <class T>
 void launch_quantise(const T *C, long long ldc, int nB, int nA, int ldq, double eps, uint16_t *cb,
                      WsHead *head, int grid, cudaStream_t st) {
-    const float inv_eps = (float)(1.0 / eps);
+    const EpsSplit e = make_eps_split(eps);
     const bool vec = ((uintptr_t)C % 16 == 0) && ((ldc * (long long)sizeof(T)) % 16 == 0);
-    if (vec) k_quantise<T, true><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, eps, inv_eps, cb, head);
-    else k_quantise<T, false><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, eps, inv_eps, cb, head);
+    if (vec) k_quantise<T, true><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
+    else k_quantise<T, false><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
 }
 
 }  // namespace

@@ -6,63 +6,103 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace prot {
 
 constexpr uint16_t kPadCost = 0x7FFF;  // cbar of padding columns
 constexpr uint16_t kPadKey = 0x8000;   // k of padding columns: pad sum 0xFFFF never matches
 
+// eps split exactly as me * 2^ee (me < 2^53, an integer), plus the FP32
+// reciprocal used for the estimate.  Built on the host by make_eps_split.
+struct EpsSplit {
+    unsigned long long me;
+    int ee;
+    float inv;
+};
+
+inline EpsSplit make_eps_split(double eps) {  // eps normal, in (0, 1)
+    unsigned long long bits;
+    memcpy(&bits, &eps, sizeof bits);
+    EpsSplit e;
+    e.me = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    e.ee = (int)((bits >> 52) & 0x7FF) - 1075;
+    e.inv = (float)(1.0 / eps);
+    return e;
+}
+
+// Exact test c >= m * eps for c = mc * 2^ec (mc < 2^53) and 1 <= m < 2^16,
+// in 128-bit integer arithmetic: both sides are brought to the smaller
+// exponent and compared.  Outside the shifts that fit in 128 bits the
+// answer follows from the exponents alone (c is normal, so 2^23 <= mc for
+// FP32 and 2^52 <= mc for FP64; 2^52 <= m * me < 2^69).
+__device__ __forceinline__ bool ge_multiple(unsigned long long mc, int ec, uint32_t m, const EpsSplit &e) {
+    const int d = ec - e.ee;
+    if (d > 74) return true;
+    if (d < -58) return false;
+    unsigned __int128 lhs = mc, rhs = (unsigned __int128)e.me * m;
+    if (d >= 0) lhs <<= d;
+    else rhs <<= -d;
+    return lhs >= rhs;
+}
+
 // Eq. (1) exactly: cbar = the largest k with k * eps <= c, for 0 <= c <= 1.
 // An FP32 estimate q of c/eps is within 0.008 of the exact quotient (see
 // below), so floor(q) is exact whenever q is at least 1/64 away from an
-// integer.  Otherwise the integer is settled with fma(-k, eps, c), whose sign
-// is that of the exact c - k*eps.  No FP64 division runs per element.
+// integer.  Otherwise the exact quotient lies within 0.03 of the integer m
+// nearest q, so the floor is m or m - 1, settled by the exact integer test
+// c >= m * eps.  No floating-point division and no FP64 instruction runs
+// (GB300 runs FP64 at a small fraction of its FP32 rate).
 //
-// For an FP64 cost given by its bit pattern, with no FP64
-// instruction on the common path (GB300 runs FP64 at a small fraction of its
-// FP32 rate).  Range test on the bits: 0 <= c <= 1 (or -0.0), which also
-// rejects NaN and infinities.  The FP32 estimate truncates the mantissa
-// (relative error < 2^-23) before the two roundings of the product, so q is
-// within 0.008 of the exact quotient and the 1/64 margin still holds.
+// For an FP64 cost given by its bit pattern.  Range test on the bits:
+// 0 <= c <= 1 (or -0.0), which also rejects NaN and infinities.  The FP32
+// estimate truncates the mantissa (relative error < 2^-23) before the two
+// roundings of the product, so q is within 0.008 of the exact quotient
+// (which is below 2^15) and the 1/64 margin holds.
 // Returns 0xFFFFFFFF for a cost outside [0, 1].
-__device__ __forceinline__ uint32_t quantise_bits(uint32_t hi, uint32_t lo, double eps, float inv_eps) {
+__device__ __forceinline__ uint32_t quantise_bits(uint32_t hi, uint32_t lo, const EpsSplit &e) {
     if (hi >= 0x80000000u) {  // sign bit: only -0.0 is valid
         return (hi == 0x80000000u && lo == 0u) ? 0u : 0xFFFFFFFFu;
     }
     if (hi > 0x3FF00000u || (hi == 0x3FF00000u && lo != 0u)) return 0xFFFFFFFFu;  // > 1, NaN, inf
-    const uint32_t e = hi >> 20;
-    if (e <= 896u) {
+    const uint32_t ex = hi >> 20;
+    if (ex <= 896u) {
         // c < 2^-126 (zero or tiny): floor(c / eps) is 0 unless eps is tinier,
         // which eps >= 1/32767 rules out
         return 0u;
     }
-    const uint32_t fbits = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    const float q = __fmul_rn(__uint_as_float(fbits), inv_eps);
+    const uint32_t fbits = ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const float q = __fmul_rn(__uint_as_float(fbits), e.inv);
     const float kf = floorf(q);
     const float fr = q - kf;
-    int k = (int)kf;
+    uint32_t k = (uint32_t)kf;
     if (!(fr >= 0.015625f && fr <= 0.984375f)) {
-        const double c = __hiloint2double((int)hi, (int)lo);
-        while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
-        while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
+        const uint32_t m = k + (fr > 0.5f ? 1u : 0u);
+        if (m == 0u) return 0u;
+        const unsigned long long mc = (((unsigned long long)(hi & 0xFFFFFu) << 32) | lo) | (1ull << 52);
+        k = ge_multiple(mc, (int)ex - 1075, m, e) ? m : m - 1u;
     }
-    return (uint32_t)k;
+    return k;
 }
 
-// The same for an FP32 cost: range test on the bits, exact FP32 estimate.
-__device__ __forceinline__ uint32_t quantise_fbits(uint32_t fb, double eps, float inv_eps) {
+// The same for an FP32 cost: range test on the bits, exact FP32 estimate,
+// the same integer test near a multiple of eps.
+__device__ __forceinline__ uint32_t quantise_fbits(uint32_t fb, const EpsSplit &e) {
     if (fb >= 0x80000000u) return fb == 0x80000000u ? 0u : 0xFFFFFFFFu;
     if (fb > 0x3F800000u) return 0xFFFFFFFFu;
-    const float q = __fmul_rn(__uint_as_float(fb), inv_eps);
+    const uint32_t ex = fb >> 23;
+    if (ex == 0u) return 0u;  // zero or subnormal: below eps >= 1/32767
+    const float q = __fmul_rn(__uint_as_float(fb), e.inv);
     const float kf = floorf(q);
     const float fr = q - kf;
-    int k = (int)kf;
+    uint32_t k = (uint32_t)kf;
     if (!(fr >= 0.015625f && fr <= 0.984375f)) {
-        const double c = (double)__uint_as_float(fb);
-        while (k > 0 && fma(-(double)k, eps, c) < 0.0) --k;
-        while (fma(-(double)(k + 1), eps, c) >= 0.0) ++k;
+        const uint32_t m = k + (fr > 0.5f ? 1u : 0u);
+        if (m == 0u) return 0u;
+        const unsigned long long mc = (unsigned long long)((fb & 0x7FFFFFu) | 0x800000u);
+        k = ge_multiple(mc, (int)ex - 150, m, e) ? m : m - 1u;
     }
-    return (uint32_t)k;
+    return k;
 }
 
 // Bit j of the result: 16-bit lane j of the 8-lane vector s equals t (t2 =

@@ -49,7 +49,7 @@ def assert_parity(got, ref):
     assert abs(got["cost"] - ref["cost"]) <= COST_RTOL * max(abs(ref["cost"]), 1e-300)
 
 
-@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("seed", range(30))
 def test_config_n1000_sq_euclid(prot, seed):
     C = W.assignment_sq_euclid_2d(1000, seed)
     assert_parity(gpu_solve(prot, C, 0.1), oracle.assign(C, 0.1))
@@ -121,6 +121,37 @@ def test_full_size_n10000(prot, eps):
     bench times, compared in full with the oracle."""
     C = W.assignment_euclid_2d(10000, 0)
     assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+def dual_certificate(C, eps, got):
+    """Lemma 3.1 on the GPU's own duals, a check that needs no optimum:
+    Eq. (2) and (3) hold on every edge (in units of eps) for the matching
+    before completion, and c(M) <= L + 2 eps n_B + T with
+    L = eps (sum y - n_B) a lower bound on OPT."""
+    nB = C.shape[0]
+    yb = got["y_row"].astype(np.int64)
+    ya = got["y_col"].astype(np.int64)
+    assert yb.min() >= 1 and ya.max() <= 0
+    T = oracle.threshold(eps, nB)
+    for r0 in range(0, nB, 1000):  # row blocks keep the host memory small
+        cb = oracle.quantise(C[r0:r0 + 1000], eps).astype(np.int64)
+        s = cb + 1 - yb[r0:r0 + 1000, None] - ya[None, :]
+        assert s.min() >= 0                                   # Eq. (2)
+        m = got["row_to_col"][r0:r0 + 1000]
+        tight = s[np.arange(len(m)), m] == 1                  # Eq. (3)
+        assert (~tight).sum() <= T  # only completion edges may break it
+    L = eps * (yb.sum() + ya.sum() - nB)
+    assert got["cost"] <= L + 2 * eps * nB + T + 1e-6
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_full_size_n10000_more_seeds(prot, seed):
+    """Five more seeds of the n = 10,000 workload at eps = 0.01: parity in
+    full, and the dual certificate on the GPU's duals."""
+    C = W.assignment_euclid_2d(10000, seed)
+    got = gpu_solve(prot, C, 0.01)
+    assert_parity(got, oracle.assign(C, 0.01))
+    dual_certificate(C, 0.01, got)
 
 
 def test_repeat_is_deterministic(prot):
