@@ -56,6 +56,8 @@ typedef struct {
     int64_t rows_scanned;  /* row scans started (one per free vertex per round) */
     int32_t free_at_stop;  /* |B'| when the loop stopped (<= threshold)         */
     int32_t threshold;     /* T = floor(eps * n_rows)                           */
+    int32_t loop_ctas;     /* CTAs that ran the phase loop (0: not applicable)  */
+    int32_t loop_cluster;  /* 1: they formed one thread-block cluster; 0: grid  */
 } pr_stats;
 
 /*

@@ -32,6 +32,8 @@ class PrStats(ctypes.Structure):
         ("rows_scanned", ctypes.c_int64),
         ("free_at_stop", ctypes.c_int32),
         ("threshold", ctypes.c_int32),
+        ("loop_ctas", ctypes.c_int32),
+        ("loop_cluster", ctypes.c_int32),
     ]
 
     def as_dict(self):

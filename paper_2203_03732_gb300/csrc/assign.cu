@@ -2,7 +2,8 @@
 //
 // Pipeline (all on the caller's stream, no host round trip inside a solve):
 //   k_init      y(b) = 1, y(a) = 0, M empty                        (Sec. 2.2)
-//   k_quantise  cbar = floor(c / eps) exactly, uint16, [b][a]      (Eq. 1)
+//   k_quantise  cbar = floor(c / eps) exactly, [b][a]: uint8 when
+//               floor(1/eps) <= 254, else uint16                   (Eq. 1)
 //   k_phases    persistent cooperative kernel: every phase and round
 //   k_decode    matching and y(A) out of the per-column words
 //   k_finish    completion + FP64 cost                             (Sec. 2.1)
@@ -11,7 +12,10 @@
 // (slack 0, Eq. 2 with equality) iff  cbar(b,a) + k(a) == y(b) - 1.  Both
 // cbar and k fit 16 bits (Lemma 3.2 bounds |y| by floor(1/eps) + 2), so one
 // 16-byte load of eight cbar values meets eight k values in four 32-bit adds
-// (two 16-bit lanes per word, no carry between them).
+// (two 16-bit lanes per word, no carry between them).  When cbar <= 254 it is
+// stored in one byte: the matrix is half the size (100 MB at n = 10,000,
+// inside the 126 MB L2, so the later phases' rescans hit L2 instead of HBM),
+// and each 16-byte load brings sixteen values, widened to 16-bit lanes.
 //
 // One 64-bit word per column carries all of step (I) and the matching:
 //   word(a) = (R << 32) | (0xFFFFFFFF - b)
@@ -36,6 +40,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "prot_internal.cuh"
@@ -48,7 +53,15 @@ namespace {
 constexpr int kThreads = 512;             // threads per CTA of the phase kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kUnroll = 8;                // 16-byte loads in flight per lane per chunk
-constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk (4 KiB)
+// cbar elements per 16-byte load and per warp chunk (32 lanes x kUnroll
+// loads: 4 KiB) for the storage type CB
+template <class CB> constexpr int kPerLoad = 16 / (int)sizeof(CB);
+template <class CB> constexpr int kChunk = 32 * kPerLoad<CB> * kUnroll;
+// Byte form: used when floor(1/eps) <= 252.  cbar <= 252, every key
+// k(a) <= floor(1/eps) + 2 <= 254 (Lemma 3.2) and every target y(b) - 1 <=
+// 253, so a saturating byte add cbar + k that reaches 255 can never equal a
+// target, and 255 pads both cbar and keys.
+constexpr int kMaxCbar8 = 252;
 constexpr int kListSm = 1024;             // proposal-list entries kept in shared memory
 constexpr int kKeepMax = 16;              // rows a CTA may keep for its next phase
 constexpr int kBatch = 256;               // items turned into scan jobs at a time
@@ -89,9 +102,9 @@ struct Layout {
 Layout make_layout(int nB, int nA, int grid) {
     Layout L;
     Carver c;
-    L.ldq = (nA + 7) & ~7;
+    L.ldq = (nA + 15) & ~15;  // rows start on 16 bytes in either storage type
     L.ctl = c.take<Ctl>(1);
-    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
+    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);  // room for the uint16 form
     L.ka = c.take<uint16_t>(L.ldq);
     L.prop = c.take<unsigned long long>((size_t)nA);
     L.won_words = (nA + 31) / 32;
@@ -105,19 +118,21 @@ Layout make_layout(int nB, int nA, int grid) {
 
 struct Params {
     Ctl *ctl;
-    const uint16_t *cb;
+    const void *cb;  // uint8_t or uint16_t [nB][ldq], as the kernel is instantiated
     uint16_t *ka;
     int *y_b;
     unsigned long long *prop;
     unsigned *won;  // [3][won_words] first proposals of rounds R % 3
     int won_words;
-    int2 *pool;  // [2][nB] (b, y(b) or -1)
+    int2 *pool;  // [2][nB] (b, y(b)) or, for an evicted row, (b, -1 - resume column)
     int *lists;
     size_t list_stride;
     int nB, nA, ldq, T;
     long long phase_cap;
     long long spin_limit;
     int profile;
+    int nslots;        // cluster mode: row slots in shared memory (one per scanning warp)
+    int slot_bytes;    // bytes per row slot (a whole cbar row, 128-byte multiple)
 };
 
 // ---------------------------------------------------------------------------
@@ -148,33 +163,58 @@ __global__ void k_init(Params p, int *match_b) {
 // phase nothing is taken; in later rounds a candidate column is skipped when
 // its word carries a tag of an earlier round of this phase.
 // ---------------------------------------------------------------------------
-// Lowest candidate column in [c0, c0 + kChunk) that is >= start and not in the
-// phase's taken set tk (shared memory; empty in a phase's first round), or -1.
-__device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row, const uint16_t *ks,
+// Sum of 8 cbar values (packed 16-bit lanes) and their keys, from one
+// 16-byte load of uint16 cbar, or from half of a 16-byte load of uint8 cbar
+// (bytes widened to 16-bit lanes: byte j of x goes to lane j).
+__device__ __forceinline__ uint4 add_keys(uint4 c, uint4 k) {
+    return make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
+}
+__device__ __forceinline__ uint4 widen_lo(uint4 x) {
+    return make_uint4(__byte_perm(x.x, 0, 0x4140), __byte_perm(x.x, 0, 0x4342),
+                      __byte_perm(x.y, 0, 0x4140), __byte_perm(x.y, 0, 0x4342));
+}
+__device__ __forceinline__ uint4 widen_hi(uint4 x) {
+    return make_uint4(__byte_perm(x.z, 0, 0x4140), __byte_perm(x.z, 0, 0x4342),
+                      __byte_perm(x.w, 0, 0x4140), __byte_perm(x.w, 0, 0x4342));
+}
+
+// Lowest candidate column in [c0, c0 + kChunk<CB>) that is >= start and not
+// in the phase's taken set tk (shared memory; empty in a phase's first
+// round), or -1.  Lane l covers kPerLoad<CB> consecutive columns of each of
+// the kUnroll loads, all issued before any is used.
+template <class CB>
+// tgt_in < 0: the row's y(b) is not known yet (an evicted row); lane 0 reads
+// it after the row loads are issued, so the two reads overlap.  The target
+// used comes back in tgt_out.
+__device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const CB *ks,
                                                const unsigned *tk, bool check_taken, int c0,
-                                               int start, int ldq, uint32_t tgt, int lane) {
-    uint4 sv[kUnroll];
+                                               int start, int ldq, int tgt_in, const int *yb,
+                                               int &tgt_out, int lane) {
+    constexpr int W = kPerLoad<CB>;
+    constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
+    uint4 cv[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-        const int idx = c0 + u * 256 + lane * 8;
-        if (idx < ldq) {
-            const uint4 c = ld_nc_na_v4(row + idx);
-            const uint4 k = *reinterpret_cast<const uint4 *>(ks + idx);
-            sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
-        } else {
-            sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        }
+        const int idx = c0 + u * 32 * W + lane * W;
+        cv[u] = idx < ldq ? ld_nc_na_v4(row + idx) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
     }
-    const uint32_t t2 = tgt | (tgt << 16);
+    const int tg = tgt_in >= 0 ? tgt_in : __shfl_sync(0xFFFFFFFFu, lane == 0 ? ld_relaxed_s32(yb) - 1 : 0, 0);
+    tgt_out = tg;
+    const uint32_t tgt = (uint32_t)tg;
+    const uint32_t t2 = W == 8 ? (tgt | (tgt << 16)) : tgt * 0x01010101u;
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-        const int idx = c0 + u * 256 + lane * 8;
-        unsigned m = eq_mask(sv[u], t2);
+        const int idx = c0 + u * 32 * W + lane * W;
+        unsigned m = 0;
+        if (idx < ldq) {
+            const uint4 kv = *reinterpret_cast<const uint4 *>(ks + idx);
+            m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8(cv[u], kv, t2);
+        }
         const int lo = start - idx;
-        if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+        if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
         if (check_taken && m) {
-            // 8 columns idx..idx+7 lie in one 32-bit word of the bitmap
-            m &= ~(tk[idx >> 5] >> (idx & 31)) & 0xFFu;
+            // the W columns idx .. idx + W - 1 lie in one 32-bit word of the bitmap
+            m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
         }
         const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
         if (any == 0) continue;
@@ -190,13 +230,13 @@ __device__ __forceinline__ int warp_scan_chunk(const uint16_t *__restrict__ row,
 // CTA's private region of the workspace.
 // ---------------------------------------------------------------------------
 struct Smem {
-    int2 fl[2][kKeepMax];     // kept (b, y(b) or -1) of this phase / next phase
+    int2 fl[2][kKeepMax];     // kept rows of this phase / next phase, as pool entries
     int4 ql[2][kListSm];      // (b, a, y(b)) proposals of this round / previous round
     int job_b[kBatch];
     int job_start[kBatch];
     int job_tgt[kBatch];
     int job_best[kBatch];
-    int2 don[kBatch];         // (b, y(b) or -1) given to the pool in this batch
+    int2 don[kBatch];         // pool entries given to the pool in this batch
     int best[kWarps];
     int nfl[2], nql[2];
     int njob, ndon, don_base;
@@ -205,6 +245,8 @@ struct Smem {
     unsigned long long rows;
     unsigned long long pub, pub2;
     unsigned long long pacc[4];  // profile: build, scan, proposal, tail ns of this round
+    unsigned long long cbar[4][2];  // cluster mode: this CTA's copy of the barrier slots
+    unsigned long long mbar[kWarps];  // cluster mode: completion of each warp's row copy
     int err;
 };
 
@@ -278,19 +320,194 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
     return s.err == 0;
 }
 
-// The queued jobs: one parallel read of every job's y(b); then the row scans,
-// rows_per_group rows at a time with warps_per_row warps per row; then every
-// proposal (atomicMax) or relabel at once; then the pool donations.
+// Cluster form of grid_sync, for a launch that is one thread-block cluster.
+// Every CTA holds its own copy of the four slots in shared memory.  At
+// barrier h lane r of warp 0 adds the CTA's word 1 and (release, cluster
+// scope) word 0 to slot h % 4 of CTA r; thread 0 then polls its own copy
+// (bounded, acquire).  Each CTA zeroes its own slot (h + 2) % 4 during round
+// h: its last use (barrier h - 2) is over, and no CTA adds to it before
+// barrier h + 1 has completed, which needs this CTA's arrival.
+__device__ __forceinline__ uint32_t dsmem_addr(const void *p, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier_hw() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ bool cluster_sync(Ctl *ctl, Smem &s, unsigned &gen, unsigned G, long long limit,
+                                             unsigned long long mine, unsigned long long donated) {
+    __syncthreads();
+    const unsigned h = gen + 1;
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            s.cbar[(h + 2) & 3][0] = 0;
+            s.cbar[(h + 2) & 3][1] = 0;
+        }
+        if (threadIdx.x < G) {
+            const uint32_t r = dsmem_addr(&s.cbar[h & 3][0], threadIdx.x);
+            if (donated)
+                asm volatile("red.relaxed.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(r + 8), "l"(donated) : "memory");
+            asm volatile("red.release.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(r), "l"(mine) : "memory");
+        }
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t self = dsmem_addr(&s.cbar[h & 3][0], blockIdx.x);
+        unsigned long long v = 0;
+        const long long t0 = clock64();
+        bool ok = true;
+        for (;;) {
+            asm volatile("ld.acquire.cluster.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(self) : "memory");
+            if ((v & 1023ull) == (unsigned long long)G) break;
+            if (ld_relaxed_s32(&ctl->head.abort)) {
+                ok = false;
+                break;
+            }
+            if (clock64() - t0 > limit) {
+                record_error(&ctl->head, PR_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+        }
+        const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
+        s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
+        unsigned long long d = 0;
+        if (ok) asm volatile("ld.relaxed.cluster.shared::cluster.u64 %0, [%1];" : "=l"(d) : "r"(self + 8) : "memory");
+        s.pub2 = d;
+        s.err = ok ? 0 : 1;
+    }
+    __syncthreads();
+    gen += 1;
+    return s.err == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Cluster-mode row scan: the row's tail [s_al, ldq) is copied by one bulk
+// (TMA) copy into the warp's shared-memory slot, then scanned there.  With one
+// slot per warp an SM keeps up to 16 rows (160 KB at n = 10,000) in flight,
+// which the 16-byte register loads of the grid form cannot: per SM those
+// reach about 64 GB/s from L2, bulk copies about 120 GB/s.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_row_copy(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+    // order this warp's earlier reads of the slot (generic proxy) before the
+    // copy's writes (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
+}
+
+// Waits (bounded by `limit` cycles) for the phase of parity `parity` of mbar.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                     : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// Lowest candidate column >= start in the slot holding cbar[s_al .. ldq) of
+// one row (the test of warp_scan_chunk), or -1.  Four 16-byte shared loads
+// per lane are in flight per step.
+template <class CB>
+__device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const CB *ks, const unsigned *tk,
+                                              bool check_taken, int s_al, int start, int ldq, uint32_t tgt,
+                                              int lane) {
+    constexpr int W = kPerLoad<CB>;
+    constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
+    constexpr int kU = 4;
+    const uint32_t t2 = W == 8 ? (tgt | (tgt << 16)) : tgt * 0x01010101u;
+    for (int e0 = s_al; e0 < ldq; e0 += kU * 32 * W) {
+        uint4 cv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = e0 + u * 32 * W + lane * W;
+            cv[u] = idx < ldq ? *reinterpret_cast<const uint4 *>(slot + (size_t)(idx - s_al) * sizeof(CB))
+                              : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = e0 + u * 32 * W + lane * W;
+            unsigned m = 0;
+            if (idx < ldq) {
+                const uint4 kv = *reinterpret_cast<const uint4 *>(ks + idx);
+                m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8(cv[u], kv, t2);
+            }
+            const int lo = start - idx;
+            if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
+            if (check_taken && m) m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
+            const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
+            if (any == 0) continue;
+            const int L = __ffs(any) - 1;
+            const int a = idx + __ffs(m) - 1;  // meaningful in lane L
+            return __shfl_sync(0xFFFFFFFFu, a, L);
+        }
+    }
+    return -1;
+}
+
+// A bulk copy's completion wait: long enough for any copy a working GPU
+// finishes (about a second), independent of the barrier spin limit.
+constexpr long long kCopyWaitCycles = 2000000000ll;
+
+// The queued jobs: the row scans (grid form: rows_per_group rows at a time
+// with warps_per_row warps per row; cluster form: one row per warp through
+// its slot); then every proposal (atomicMax) or relabel at once; then the
+// pool donations.
+template <class CB, bool CL>
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
-                                         const uint16_t *ks, const unsigned *tk, unsigned *won_now,
+                                         const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
                                          int2 *pool_next, int *pool_cnt, int warps_per_row,
-                                         int rows_per_group) {
+                                         int rows_per_group, unsigned char *slots, unsigned &mstate) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
     const unsigned long long tA = p.profile ? gtimer() : 0;
-    for (int j = threadIdx.x; j < nq; j += blockDim.x)
-        if (s.job_tgt[j] < 0) s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
+    // cluster form: every unknown y(b) is read here (the grid form reads it
+    // inside the row scan)
+    if (CL)
+        for (int j = threadIdx.x; j < nq; j += blockDim.x)
+            if (s.job_tgt[j] < 0) s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
+    if (CL) {
+        // warp w scans jobs w, w + nslots, ... through its own slot
+        __syncthreads();
+        unsigned long long my_bytes = 0;
+        // mstate: bit 0 the parity of the warp's next mbarrier phase; bit 1 a
+        // copy whose completion was not seen (after a wait gave up: no more
+        // copies, the solve reports PR_ERR_TIMEOUT)
+        if (warp < p.nslots) {
+            unsigned char *slot = slots + (size_t)warp * p.slot_bytes;
+            for (int j = warp; j < nq; j += p.nslots) {
+                const int b = s.job_b[j];
+                const int start = s.job_start[j];
+                const int s_al = start & ~(kPerLoad<CB> - 1);
+                const uint32_t tgt = (uint32_t)s.job_tgt[j];
+                int a = -1;
+                if (s_al < p.ldq && !(mstate & 2u)) {
+                    const unsigned bytes = (unsigned)((p.ldq - s_al) * sizeof(CB));
+                    const CB *src = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq + s_al;
+                    __syncwarp();
+                    if (lane == 0) bulk_row_copy(slot, src, bytes, &s.mbar[warp]);
+                    if (mbar_wait(&s.mbar[warp], mstate & 1u, kCopyWaitCycles)) {
+                        mstate ^= 1u;
+                        my_bytes += bytes;
+                        a = warp_scan_slot<CB>(slot, ks, tk, R > Rps, s_al, start, p.ldq, tgt, lane);
+                    } else {
+                        mstate |= 2u;
+                        if (lane == 0) record_error(&p.ctl->head, PR_ERR_TIMEOUT);
+                    }
+                }
+                if (lane == 0) s.job_best[j] = a >= 0 ? a : 0x7FFFFFFF;
+            }
+        }
+        if (lane == 0 && my_bytes) atomicAdd(&s.bytes, my_bytes);
+    } else
     for (int g0 = 0; g0 < nq; g0 += rows_per_group) {
         const int ng = min(rows_per_group, nq - g0);
         if (threadIdx.x < ng) s.best[threadIdx.x] = 0x7FFFFFFF;
@@ -300,20 +517,27 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (slot < ng) {
             const int b = s.job_b[g0 + slot];
             const int start = s.job_start[g0 + slot];
-            const int s8 = start & ~7;
-            const uint32_t tgt = (uint32_t)s.job_tgt[g0 + slot];
-            const uint16_t *row = p.cb + (size_t)b * p.ldq;
+            const int s_al = start & ~(kPerLoad<CB> - 1);
+            int tgt = s.job_tgt[g0 + slot];
+            const CB *row = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq;
             volatile int *vbest = &s.best[slot];
-            for (int c0 = s8 + sub * kChunk; c0 < p.ldq; c0 += warps_per_row * kChunk) {
+            const bool known = tgt >= 0;
+            for (int c0 = s_al + sub * kChunk<CB>; c0 < p.ldq; c0 += warps_per_row * kChunk<CB>) {
                 // warp-uniform early exit: lane 0's view of the row's best so far
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
-                my_bytes += 2ull * (unsigned long long)min(kChunk, p.ldq - c0);
-                const int a = warp_scan_chunk(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, lane);
+                my_bytes += sizeof(CB) * (unsigned long long)min(kChunk<CB>, p.ldq - c0);
+                int t_used;
+                const int a = warp_scan_chunk<CB>(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, p.y_b + b,
+                                                  t_used, lane);
+                tgt = t_used;
                 if (a >= 0) {
                     if (lane == 0) atomicMin(&s.best[slot], a);
                     break;
                 }
             }
+            // the proposal step needs y(b): the first sub-warp stores what it read
+            if (!known && sub == 0 && lane == 0)
+                s.job_tgt[g0 + slot] = tgt >= 0 ? tgt : ld_relaxed_s32(p.y_b + b) - 1;
         }
         if (lane == 0 && my_bytes) atomicAdd(&s.bytes, my_bytes);
         __syncthreads();
@@ -336,7 +560,12 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 // +1 on the 16-bit output key at L2 (no carry leaves the half: k <= 32768)
                 atomicAdd(reinterpret_cast<unsigned *>(p.ka + (a & ~1)), (a & 1) ? 0x10000u : 1u);
                 const int partner = row_of(old);
-                if (partner >= 0) push_next(s, nxt, keep, partner, -1);
+                // The evicted row keeps y(b), and every column <= a is above
+                // its target for good (its scan that reached a found nothing
+                // admissible before a; keys only rise), so its next scan starts
+                // at a + 1.  Its y(b) is not known here: the entry carries
+                // -1 - (a + 1) instead.
+                if (partner >= 0) push_next(s, nxt, keep, partner, -2 - a);
             } else if (t == R) {
                 s.nonfirst = 1;
             } else {
@@ -385,12 +614,27 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
 // otherwise each CTA rereads its proposals' words to find the losers and runs
 // round R + 1.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of the phase kernel: Smem, the key copy, the taken
+// set; in cluster mode then row slots from a 128-byte boundary.
+__host__ __device__ inline size_t smem_bytes(int ldq, int key_bytes = 2) {
+    return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)ldq * key_bytes +
+           (size_t)((ldq + 31) / 32) * sizeof(unsigned);
+}
+__host__ __device__ inline size_t slots_offset(int ldq, int key_bytes) {
+    return (smem_bytes(ldq, key_bytes) + 127) & ~size_t(127);
+}
+
+template <class CB, bool CL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
     Smem &s = *reinterpret_cast<Smem *>(dyn);
-    uint16_t *ks = reinterpret_cast<uint16_t *>(dyn + ((sizeof(Smem) + 15) & ~size_t(15)));
+    // key copy k(A) in the storage type of cbar (bytes: padding 0xFF)
+    CB *ks = reinterpret_cast<CB *>(dyn + ((sizeof(Smem) + 15) & ~size_t(15)));
     unsigned *tk = reinterpret_cast<unsigned *>(ks + p.ldq);  // taken set of the phase
+    // cluster mode: row slots after the taken set, 128-byte aligned
+    unsigned char *slots = dyn + slots_offset(p.ldq, (int)sizeof(CB));
+    unsigned mstate = 0;  // cluster mode: this warp's copy state (see run_jobs)
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
@@ -400,16 +644,42 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     g.ql[0] = reinterpret_cast<int4 *>(base);
     g.ql[1] = reinterpret_cast<int4 *>(base + 4 * (size_t)p.nB);
 
-    for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x)
-        reinterpret_cast<uint4 *>(ks)[i] = reinterpret_cast<const uint4 *>(p.ka)[i];
+    for (int i = threadIdx.x; i < (p.ldq >> 3); i += blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4 *>(p.ka)[i];
+        if (sizeof(CB) == 2) {
+            reinterpret_cast<uint4 *>(ks)[i] = v;
+        } else {  // eight 16-bit keys to bytes; the padding key 0x8000 becomes 0xFF
+            uint32_t w[4] = {v.x, v.y, v.z, v.w}, o[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t k16 = (w[2 * h + q / 2] >> (16 * (q & 1))) & 0xFFFFu;
+                    r |= (k16 > 0xFFu ? 0xFFu : k16) << (8 * q);
+                }
+                o[h] = r;
+            }
+            reinterpret_cast<uint2 *>(ks)[i] = make_uint2(o[0], o[1]);
+        }
+    }
     for (int i = threadIdx.x; i < p.won_words; i += blockDim.x) tk[i] = 0;
     if (threadIdx.x == 0) {
         s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
         s.njob = s.ndon = 0;
         s.bytes = s.rows = 0;
         s.err = 0;
+        for (int i = 0; i < 4; ++i) s.cbar[i][0] = s.cbar[i][1] = 0;
+        if (CL) {
+            for (int w = 0; w < p.nslots; ++w)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s.mbar[w])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     __syncthreads();
+    // Cluster mode: no CTA adds to another's barrier slots before all have
+    // started and zeroed them.
+    if (CL) cluster_barrier_hw();
 
     unsigned gen = 0;
     unsigned R = 0;  // global round counter (round tags)
@@ -469,7 +739,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                         m |= tk[i];
                         tk[i] = 0;
                         while (m) {
-                            ks[i * 32 + __ffs(m) - 1] += 1;
+                            ks[i * 32 + __ffs(m) - 1] += (CB)1;
                             m &= m - 1;
                         }
                     } else {
@@ -503,6 +773,10 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                             b = e.x;
                             y = e.y;
                         }
+                        if (y < 0) {  // an evicted row: y(b) unknown, resume point -1 - y
+                            start = -1 - y;
+                            y = -1;
+                        }
                     } else {
                         const int4 q = pre ? pre_q : ql_get(s, g, qcur ^ 1, it);
                         const unsigned long long w = pre ? pre_word : ld_relaxed_u64(p.prop + q.y);
@@ -518,8 +792,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 }
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += gtimer() - t_mark;
-                run_jobs(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
-                         &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group);
+                run_jobs<CB, CL>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
+                                 &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate);
                 if (p.profile) t_mark = gtimer();
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
@@ -542,7 +816,9 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     for (int k = 0; k < kProfSegs; ++k) ctl->prof_slot[(R + 1) & 1][k] = 0;
                 }
             }
-            if (!grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)) goto done;
+            const bool synced = CL ? cluster_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)
+                                   : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated);
+            if (!synced) goto done;
             if (p.profile && threadIdx.x == 0) {
                 seg[5] = gtimer() - t_r2;
                 // the barrier segment of round R goes to the next round's slot
@@ -587,6 +863,16 @@ done:
             ctl->phases = phase;
             ctl->rounds = rounds;
         }
+    }
+    // Cluster mode: a CTA's shared memory must outlive every add another CTA
+    // makes to it.  Every CTA gets here: the loop ends on the same shared
+    // decision everywhere, or on a bounded wait that gave up.
+    if (CL) {
+        // a copy whose wait gave up gets one more bounded wait: the CTA must
+        // not exit while it may still write the slot
+        if (mstate & 2u) mbar_wait(&s.mbar[threadIdx.x >> 5], mstate & 1u, kCopyWaitCycles);
+        __syncthreads();
+        cluster_barrier_hw();
     }
 }
 
@@ -681,14 +967,42 @@ k_finish(Params p, const T *__restrict__ C, long long ldc, int *match_b, int *ma
 // Host side
 // ---------------------------------------------------------------------------
 struct PhaseCfg {
-    int grid = 0;
+    int grid = 0;     // grid mode: one CTA per SM (cooperative launch)
+    int cluster = 0;  // cluster mode: CTAs in the one cluster (0: not available)
     size_t smem = 0;
 };
 
-size_t smem_bytes(int ldq) {
-    return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)ldq * sizeof(uint16_t) +
-           (size_t)((ldq + 31) / 32) * sizeof(unsigned);
+template <class CB, bool CL>
+pr_status set_phase_attrs(size_t smem) {
+    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return PR_OK;
 }
+
+// Largest cluster (16, else 8) of k_phases<CB, true> the device can hold, or 0.
+template <class CB>
+int max_phase_cluster(size_t smem) {
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t c = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        c.gridDim = dim3(cs);
+        c.blockDim = dim3(kThreads);
+        c.dynamicSmemBytes = smem;
+        c.attrs = at;
+        c.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true>, &c) == cudaSuccess && n >= 1)
+            return cs;
+        cudaGetLastError();  // clear a refusal of this size
+    }
+    return 0;
+}
+
+
 
 pr_status phase_cfg(PhaseCfg &cfg) {
     static int cached_dev = -1;
@@ -701,16 +1015,152 @@ pr_status phase_cfg(PhaseCfg &cfg) {
     }
     const DeviceInfo &di = device_info();
     const size_t smem = (size_t)di.max_smem_optin;  // Smem + the key copy; see smem_bytes()
-    PR_CUDA(cudaFuncSetAttribute(k_phases, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases, kThreads, smem));
+    pr_status rc = set_phase_attrs<uint8_t, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true>(smem);
+    if (rc != PR_OK) return rc;
+    int per_sm = 0, per_sm16 = 0;
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false>, kThreads, smem));
+    if (per_sm16 < per_sm) per_sm = per_sm16;
     if (per_sm < 1) return fail(PR_ERR_INVALID, "phase kernel does not fit on an SM");
     int grid = di.sms * per_sm;
     if (grid > kMaxGrid) grid = kMaxGrid;
     cfg.grid = grid;
+    const int c8 = max_phase_cluster<uint8_t>(smem), c16 = max_phase_cluster<uint16_t>(smem);
+    cfg.cluster = c8 < c16 ? c8 : c16;
     cfg.smem = smem;  // the most a launch may ask for; each launch asks smem_bytes(ldq)
     cached = cfg;
     cached_dev = dev;
+    return PR_OK;
+}
+
+// The phase loop runs in one thread-block cluster (barriers through
+// distributed shared memory, about a third of a grid barrier's latency) or
+// on the whole grid (one CTA per SM, barriers through L2).  PR_PHASE_MODE =
+// "grid" or "cluster" forces one; otherwise the cluster runs problems of up
+// to kClusterMaxRows rows.
+// Cluster mode also needs at least kMinSlots row slots next to the keys.
+constexpr int kMinSlots = 4;
+
+// Measured on GB300 (eps = 0.01): the cluster is ahead up to a few thousand
+// rows (n = 2000: 15 %, n = 4000: 6 %); at n = 10,000 the 16 SMs' scan
+// throughput falls behind the whole grid's (37 % slower).
+constexpr int kClusterMaxRows = 4096;
+
+bool use_cluster(const PhaseCfg &cfg, int nslots, int n_rows) {
+    if (cfg.cluster < 1 || nslots < kMinSlots) return false;
+    const char *m = getenv("PR_PHASE_MODE");
+    if (m && strcmp(m, "grid") == 0) return false;
+    if (m && strcmp(m, "cluster") == 0) return true;
+    return n_rows <= kClusterMaxRows;
+}
+
+// Everything after the argument checks, shared by pr_assign and
+// pr_assign_noalloc: p holds the workspace regions and sizes; this fills the
+// scalars, then enqueues init, rounding, the phase loop, decode and finish.
+pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, double eps, const PhaseCfg &cfg,
+                       int32_t *row_to_col, int32_t *col_to_row, int32_t *y_col, double *cost,
+                       pr_stats *stats, bool profile_ok, const char *who, cudaStream_t st) {
+    const int n_rows = p.nB, n_cols = p.nA;
+    p.T = (int)floor(eps * (double)n_rows);
+    const long long K = (long long)floor(1.0 / eps);
+    p.phase_cap = ((long long)n_rows * (2 * K + 3)) / (p.T + 1) + 1;
+    p.spin_limit = spin_limit_cycles();
+    p.profile = 0;
+    if (profile_ok) {
+        const char *pf = getenv("PR_PROFILE");
+        p.profile = (pf && *pf == '1') ? 1 : 0;
+    }
+    const bool cb8 = K <= kMaxCbar8;  // every cbar fits one byte
+
+    const DeviceInfo &di = device_info();
+    k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
+    PR_CUDA(cudaGetLastError());
+    const long long groups = (long long)n_rows * (p.ldq >> 3);
+    const long long want = groups / 256 + 1;
+    const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
+    void *cbw = const_cast<void *>(p.cb);
+    if (dt == PR_F64 && cb8)
+        launch_quantise<double, uint8_t>((const double *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint8_t *)cbw,
+                                         &p.ctl->head, qgrid, st);
+    else if (dt == PR_F64)
+        launch_quantise<double, uint16_t>((const double *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint16_t *)cbw,
+                                          &p.ctl->head, qgrid, st);
+    else if (cb8)
+        launch_quantise<float, uint8_t>((const float *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint8_t *)cbw,
+                                        &p.ctl->head, qgrid, st);
+    else
+        launch_quantise<float, uint16_t>((const float *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint16_t *)cbw,
+                                         &p.ctl->head, qgrid, st);
+    PR_CUDA(cudaGetLastError());
+
+    const int chunk = cb8 ? kChunk<uint8_t> : kChunk<uint16_t>;
+    const int chunks = (p.ldq + chunk - 1) / chunk;
+    int warps_per_row = chunks < kWarps ? chunks : kWarps;
+    int rows_per_group = kWarps / warps_per_row;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (profile_ok) kernel_events(&ev0, &ev1);
+    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev0, st));
+    const size_t row_bytes = (size_t)p.ldq * (cb8 ? 1 : 2);
+    p.slot_bytes = (int)((row_bytes + 127) & ~size_t(127));
+    const int kb = cb8 ? 1 : 2;  // bytes per key in the shared-memory copy
+    const size_t slot_room = cfg.smem > slots_offset(p.ldq, kb) ? cfg.smem - slots_offset(p.ldq, kb) : 0;
+    p.nslots = (int)std::min<size_t>((size_t)kWarps, slot_room / (size_t)p.slot_bytes);
+    const bool cluster = use_cluster(cfg, p.nslots, n_rows);
+    if (cluster) {
+        cudaLaunchConfig_t c = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cfg.cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        c.gridDim = dim3(cfg.cluster);
+        c.blockDim = dim3(kThreads);
+        c.dynamicSmemBytes = slots_offset(p.ldq, kb) + (size_t)p.nslots * p.slot_bytes;
+        c.stream = st;
+        c.attrs = at;
+        c.numAttrs = 1;
+        if (cb8) PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint8_t, true>, p, warps_per_row, rows_per_group));
+        else PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint16_t, true>, p, warps_per_row, rows_per_group));
+    } else {
+        Params pc = p;
+        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
+        const void *fn = cb8 ? (const void *)k_phases<uint8_t, false> : (const void *)k_phases<uint16_t, false>;
+        PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, smem_bytes(p.ldq, kb), st));
+    }
+    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
+
+    k_decode<<<di.sms * 2, 256, 0, st>>>(p, row_to_col, col_to_row, y_col);
+    PR_CUDA(cudaGetLastError());
+    // completion scratch: the first CTA's list region (free after the loop)
+    int *free_b = p.lists;
+    int *free_a = p.lists + n_rows;
+    if (dt == PR_F64)
+        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
+                                                    free_b, free_a, cost);
+    else
+        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
+                                                   free_b, free_a, cost);
+    PR_CUDA(cudaGetLastError());
+
+    if (stats) {
+        Ctl h;
+        PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        PR_CUDA(cudaStreamSynchronize(st));
+        stats->phases = h.phases;
+        stats->rounds = h.rounds;
+        stats->bytes_scanned = (int64_t)h.bytes;
+        stats->rows_scanned = (int64_t)h.rows;
+        stats->free_at_stop = h.free_at_stop;
+        stats->threshold = p.T;
+        stats->loop_ctas = cluster ? cfg.cluster : cfg.grid;
+        stats->loop_cluster = cluster ? 1 : 0;
+        if (h.head.err != 0)
+            return fail((pr_status)h.head.err, "%s: device reported %s", who,
+                        pr_status_string((pr_status)h.head.err));
+    }
     return PR_OK;
 }
 
@@ -753,7 +1203,7 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
 
     Params p;
     p.ctl = (Ctl *)(w + L.ctl);
-    p.cb = (const uint16_t *)(w + L.cb);
+    p.cb = w + L.cb;
     p.ka = (uint16_t *)(w + L.ka);
     p.y_b = y_row;
     p.prop = (unsigned long long *)(w + L.prop);
@@ -765,71 +1215,8 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
-    p.T = (int)floor(eps * (double)n_rows);
-    const long long K = (long long)floor(1.0 / eps);
-    p.phase_cap = ((long long)n_rows * (2 * K + 3)) / (p.T + 1) + 1;
-    p.spin_limit = spin_limit_cycles();
-    {
-        const char *pf = getenv("PR_PROFILE");
-        p.profile = (pf && *pf == '1') ? 1 : 0;
-    }
-
-    const DeviceInfo &di = device_info();
-    k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
-    PR_CUDA(cudaGetLastError());
-    const long long groups = (long long)n_rows * (L.ldq >> 3);
-    const long long want = groups / 256 + 1;
-    const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
-    if (dt == PR_F64)
-        launch_quantise<double>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
-                                &p.ctl->head, qgrid, st);
-    else
-        launch_quantise<float>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
-                               &p.ctl->head, qgrid, st);
-    PR_CUDA(cudaGetLastError());
-
-    const int chunks = (L.ldq + kChunk - 1) / kChunk;
-    int warps_per_row = chunks < kWarps ? chunks : kWarps;
-    int rows_per_group = kWarps / warps_per_row;
-    cudaEvent_t ev0, ev1;
-    kernel_events(&ev0, &ev1);
-    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev0, st));
-    {
-        Params pc = p;
-        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
-        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(cfg.grid), dim3(kThreads),
-                                            args, smem_bytes(L.ldq), st));
-    }
-    if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
-
-    k_decode<<<di.sms * 2, 256, 0, st>>>(p, row_to_col, col_to_row, y_col);
-    PR_CUDA(cudaGetLastError());
-    // completion scratch: the first CTA's list region (free after the loop)
-    int *free_b = p.lists;
-    int *free_a = p.lists + n_rows;
-    if (dt == PR_F64)
-        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
-                                                    free_b, free_a, cost);
-    else
-        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
-                                                   free_b, free_a, cost);
-    PR_CUDA(cudaGetLastError());
-
-    if (stats) {
-        Ctl h;
-        PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-        PR_CUDA(cudaStreamSynchronize(st));
-        stats->phases = h.phases;
-        stats->rounds = h.rounds;
-        stats->bytes_scanned = (int64_t)h.bytes;
-        stats->rows_scanned = (int64_t)h.rows;
-        stats->free_at_stop = h.free_at_stop;
-        stats->threshold = p.T;
-        if (h.head.err != 0)
-            return fail((pr_status)h.head.err, "pr_assign: device reported %s",
-                        pr_status_string((pr_status)h.head.err));
-    }
-    return PR_OK;
+    return launch_solve(p, C, dt, ldc, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, true,
+                        "pr_assign", st);
 }
 
 // ---------------------------------------------------------------------------
@@ -858,9 +1245,9 @@ struct NoAllocLayout {
 NoAllocLayout make_noalloc_layout(int nB, int nA) {
     NoAllocLayout L;
     Carver c;
-    L.ldq = (nA + 7) & ~7;
+    L.ldq = (nA + 15) & ~15;  // rows start on 16 bytes in either storage type
     L.ctl = c.take<Ctl>(1);
-    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
+    L.cb = c.take<uint16_t>((size_t)nB * L.ldq);  // room for the uint16 form
     L.ka = c.take<uint16_t>(L.ldq);
     L.prop = c.take<unsigned long long>((size_t)nA);
     L.won_words = (nA + 31) / 32;
@@ -924,7 +1311,7 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
 
     Params p;
     p.ctl = (Ctl *)(w + L.ctl);
-    p.cb = (const uint16_t *)(w + L.cb);
+    p.cb = w + L.cb;
     p.ka = (uint16_t *)(w + L.ka);
     p.y_b = y_row;
     p.prop = (unsigned long long *)(w + L.prop);
@@ -936,58 +1323,6 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
-    p.T = (int)floor(eps * (double)n_rows);
-    const long long K = (long long)floor(1.0 / eps);
-    p.phase_cap = ((long long)n_rows * (2 * K + 3)) / (p.T + 1) + 1;
-    p.spin_limit = spin_limit_cycles();
-    p.profile = 0;
-
-    const DeviceInfo &di = device_info();
-    k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
-    PR_CUDA(cudaGetLastError());
-    const long long groups = (long long)n_rows * (L.ldq >> 3);
-    const long long want = groups / 256 + 1;
-    const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
-    if (dt == PR_F64)
-        launch_quantise<double>((const double *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
-                                &p.ctl->head, qgrid, st);
-    else
-        launch_quantise<float>((const float *)C, ldc, n_rows, n_cols, L.ldq, eps, (uint16_t *)p.cb,
-                               &p.ctl->head, qgrid, st);
-    PR_CUDA(cudaGetLastError());
-    const int chunks = (L.ldq + kChunk - 1) / kChunk;
-    int warps_per_row = chunks < kWarps ? chunks : kWarps;
-    int rows_per_group = kWarps / warps_per_row;
-    {
-        Params pc = p;
-        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
-        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_phases, dim3(cfg.grid), dim3(kThreads),
-                                            args, smem_bytes(L.ldq), st));
-    }
-    k_decode<<<di.sms * 2, 256, 0, st>>>(p, row_to_col, col_to_row, y_col);
-    PR_CUDA(cudaGetLastError());
-    int *free_b = p.lists;
-    int *free_a = p.lists + n_rows;
-    if (dt == PR_F64)
-        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
-                                                    free_b, free_a, cost);
-    else
-        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
-                                                   free_b, free_a, cost);
-    PR_CUDA(cudaGetLastError());
-    if (stats) {
-        Ctl h;
-        PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-        PR_CUDA(cudaStreamSynchronize(st));
-        stats->phases = h.phases;
-        stats->rounds = h.rounds;
-        stats->bytes_scanned = (int64_t)h.bytes;
-        stats->rows_scanned = (int64_t)h.rows;
-        stats->free_at_stop = h.free_at_stop;
-        stats->threshold = p.T;
-        if (h.head.err != 0)
-            return fail((pr_status)h.head.err, "pr_assign_noalloc: device reported %s",
-                        pr_status_string((pr_status)h.head.err));
-    }
-    return PR_OK;
+    return launch_solve(p, C, dt, ldc, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, false,
+                        "pr_assign_noalloc", st);
 }

@@ -31,6 +31,10 @@ namespace {
 constexpr int kUnroll = 8;
 constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk
 constexpr int kMaxN = 5000;               // largest problem whose state fits shared memory
+constexpr int kRowBits = 13;              // a free-list entry: row | resume column << 13
+constexpr int kRowMask = (1 << kRowBits) - 1;
+static_assert(kMaxN < (1 << kRowBits), "rows and resume columns must fit 13 bits");
+constexpr int kMaxCbarByte = 252;         // byte storage when floor(1/eps) <= 252 (as pr_assign)
 
 struct BDesc {
     long long cb_off;  // element offset of the rounded costs (row stride ldq)
@@ -74,7 +78,7 @@ struct BParams {
     const BDesc *desc;
     const int *order;
     const unsigned *maxbits;
-    const uint16_t *cb;
+    const void *cb;  // uint8_t or uint16_t, as k_bsolve is instantiated
     int nprob;
     int n_max;
     int ldq_max;
@@ -103,10 +107,23 @@ __device__ __forceinline__ int problem_of(const BDesc *d, int P, long long g) {
 // ---------------------------------------------------------------------------
 // Rounding of the packed matrices (Eq. 1, exact).
 // ---------------------------------------------------------------------------
-template <class T>
+// Eight rounded values to the stored type: uint16 (padding 0x7FFF) or, when
+// floor(1/eps) <= 252, bytes (padding 0xFF).
+template <class CB>
+__device__ __forceinline__ void store8(CB *dst, const uint32_t h[8]) {
+    if (sizeof(CB) == 1)
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
+                                                     h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
+    else
+        *reinterpret_cast<uint4 *>(dst) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+}
+template <class CB> constexpr uint32_t kPadOf = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
+
+template <class T, class CB>
 __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict__ d, int P,
                                 long long total_groups, EpsSplit e,
-                                uint16_t *__restrict__ cb, WsHead *head) {
+                                CB *__restrict__ cb, WsHead *head) {
     bool bad = false;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
          g += (long long)gridDim.x * blockDim.x) {
@@ -117,27 +134,21 @@ __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict
         const int b = (int)(lg / gpr);
         const int a0 = (int)(lg - (long long)b * gpr) << 3;
         const T *row = C + D.c_off + (long long)b * D.n;
-        uint32_t w[4];
+        uint32_t h[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t h[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int a = a0 + 2 * j + k;
-                if (a < D.n) {
-                    h[k] = quantise_elem(row, a, e);
-                    if (h[k] == 0xFFFFFFFFu) {
-                        bad = true;
-                        h[k] = 0;
-                    }
-                } else {
-                    h[k] = kPadCost;
+        for (int j = 0; j < 8; ++j) {
+            const int a = a0 + j;
+            if (a < D.n) {
+                h[j] = quantise_elem(row, a, e);
+                if (h[j] == 0xFFFFFFFFu) {
+                    bad = true;
+                    h[j] = 0;
                 }
+            } else {
+                h[j] = kPadOf<CB>;
             }
-            w[j] = h[0] | (h[1] << 16);
         }
-        *reinterpret_cast<uint4 *>(cb + D.cb_off + (long long)b * D.ldq + a0) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        store8<CB>(cb + D.cb_off + (long long)b * D.ldq + a0, h);
     }
     if (bad) record_error(head, PR_ERR_INVALID);
 }
@@ -191,10 +202,11 @@ __global__ void k_bpoints_max(const float *__restrict__ XA, const float *__restr
     }
 }
 
+template <class CB>
 __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
                                 int squared, const BDesc *__restrict__ d, int P,
                                 long long total_groups, const unsigned *__restrict__ maxbits,
-                                EpsSplit e, uint16_t *__restrict__ cb) {
+                                EpsSplit e, CB *__restrict__ cb) {
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
          g += (long long)gridDim.x * blockDim.x) {
         const int i = problem_of(d, P, g);
@@ -214,11 +226,10 @@ __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__res
                 const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
                 h[j] = quantise_fbits(__float_as_uint(c), e);
             } else {
-                h[j] = kPadCost;
+                h[j] = kPadOf<CB>;
             }
         }
-        *reinterpret_cast<uint4 *>(cb + D.cb_off + (long long)b * D.ldq + a0) =
-            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        store8<CB>(cb + D.cb_off + (long long)b * D.ldq + a0, h);
     }
 }
 
@@ -237,33 +248,34 @@ struct BShared {
 // Lowest column a >= start of the row with cbar + k(a) == tgt whose word does
 // not carry a tag in [Rps, R) (taken earlier in this phase), or -1.  UNROLL
 // 16-byte loads per lane are in flight per step.
-template <int UNROLL>
-__device__ __forceinline__ int warp_scan_row(const uint16_t *__restrict__ row, const uint16_t *ks,
+template <int UNROLL, class CB>
+__device__ __forceinline__ int warp_scan_row(const CB *__restrict__ row, const CB *ks,
                                              const unsigned long long *pw, int start, int ldq,
                                              uint32_t tgt, unsigned R, unsigned Rps, int lane,
                                              unsigned long long &bytes) {
-    const uint32_t t2 = tgt | (tgt << 16);
+    constexpr int W = 16 / (int)sizeof(CB);  // columns per 16-byte load
+    constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
+    const uint32_t t2 = W == 8 ? (tgt | (tgt << 16)) : tgt * 0x01010101u;
     const bool check_taken = R > Rps;
-    for (int c0 = start & ~7; c0 < ldq; c0 += 256 * UNROLL) {
-        uint4 sv[UNROLL];
+    for (int c0 = start & ~(W - 1); c0 < ldq; c0 += 32 * W * UNROLL) {
+        uint4 cv[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const int idx = c0 + u * 256 + lane * 8;
-            if (idx < ldq) {
-                const uint4 c = ld_nc_na_v4(row + idx);
-                const uint4 k = *reinterpret_cast<const uint4 *>(ks + idx);
-                sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
-            } else {
-                sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-            }
+            const int idx = c0 + u * 32 * W + lane * W;
+            cv[u] = idx < ldq ? ld_nc_na_v4(row + idx) : make_uint4(0, 0, 0, 0);
         }
-        bytes += 2ull * (unsigned long long)min(256 * UNROLL, ldq - c0);
+        bytes += sizeof(CB) * (unsigned long long)min(32 * W * UNROLL, ldq - c0);
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const int idx = c0 + u * 256 + lane * 8;
-            unsigned m = eq_mask(sv[u], t2);
+            const int idx = c0 + u * 32 * W + lane * W;
+            unsigned m = 0;
+            if (idx < ldq) {
+                const uint4 kv = *reinterpret_cast<const uint4 *>(ks + idx);
+                m = W == 8 ? eq_mask(make_uint4(cv[u].x + kv.x, cv[u].y + kv.y, cv[u].z + kv.z, cv[u].w + kv.w), t2)
+                           : eq_mask8(cv[u], kv, t2);
+            }
             const int lo = start - idx;
-            if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+            if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
             for (;;) {
                 const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
                 if (any == 0) break;
@@ -305,7 +317,7 @@ __device__ __forceinline__ int block_scan_excl(int flag, BShared &s) {
     return r;
 }
 
-template <int THREADS, int UNROLL>
+template <int THREADS, int UNROLL, class CB>
 __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ BShared s;
@@ -319,7 +331,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
     int2 *ql0 = reinterpret_cast<int2 *>(fl1 + nmax);
     int2 *ql1 = ql0 + nmax;
     int *won = reinterpret_cast<int *>(ql1 + nmax);
-    uint16_t *ks = reinterpret_cast<uint16_t *>(won + nmax);
+    CB *ks = reinterpret_cast<CB *>(won + nmax);  // keys in the stored type (bytes: padding 0xFF)
     int *fl[2] = {fl0, fl1};
     int2 *ql[2] = {ql0, ql1};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -339,10 +351,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
         const int pi = p.order[t];
         const BDesc D = p.desc[pi];
         const int n = D.n, ldq = D.ldq;
-        const uint16_t *cb = p.cb + D.cb_off;
+        const CB *cb = static_cast<const CB *>(p.cb) + D.cb_off;
 
         // Initialisation (Sec. 2.2): y(b) = eps, y(a) = 0, M empty, B' = B.
-        for (int a = threadIdx.x; a < ldq; a += blockDim.x) ks[a] = a < n ? 0 : kPadKey;
+        for (int a = threadIdx.x; a < ldq; a += blockDim.x) ks[a] = a < n ? (CB)0 : (CB)(sizeof(CB) == 1 ? 0xFF : kPadKey);
         for (int a = threadIdx.x; a < n; a += blockDim.x) pw[a] = word_of(0, -1);
         for (int b = threadIdx.x; b < n; b += blockDim.x) {
             yb[b] = 1;
@@ -386,7 +398,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
                 for (int it = warp; it < items; it += nwarps) {
                     int b, start = 0;
                     if (first) {
-                        b = fl[cur][it];
+                        // b, or b | (resume column << 13) for an evicted row
+                        const int e = fl[cur][it];
+                        b = e & kRowMask;
+                        start = e >> kRowBits;
                     } else {
                         const int2 q = ql[qcur ^ 1][it];
                         b = q.x;
@@ -394,8 +409,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
                         start = q.y + 1;                     // lost: resume after a
                     }
                     const uint32_t tgt = (uint32_t)(yb[b] - 1);
-                    const int a = warp_scan_row<UNROLL>(cb + (long long)b * ldq, ks, pw, start, ldq, tgt, R,
-                                                Rps, lane, my_bytes);
+                    const int a = warp_scan_row<UNROLL, CB>(cb + (long long)b * ldq, ks, pw, start, ldq, tgt, R,
+                                                            Rps, lane, my_bytes);
                     if (lane == 0) {
                         if (a >= 0) {
                             const unsigned long long old = atomicMax(pw + a, word_of(R, b));
@@ -403,8 +418,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
                                 // first proposal: a is won this round (step III a
                                 // at the phase end), its partner is evicted (II)
                                 won[atomicAdd(&s.nwon, 1)] = a;
+                                // the evicted row resumes after a: every column
+                                // <= a is above its (unchanged) target for good
                                 const int partner = row_of(old);
-                                if (partner >= 0) fl[cur ^ 1][atomicAdd(&s.nfl[cur ^ 1], 1)] = partner;
+                                if (partner >= 0)
+                                    fl[cur ^ 1][atomicAdd(&s.nfl[cur ^ 1], 1)] = partner | ((a + 1) << kRowBits);
                             } else {
                                 s.nonfirst = 1;
                             }
@@ -430,7 +448,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_bsolve(BParams p) {
                 if (!contested) break;
             }
             // step (III a): y(a) -= eps for the columns won in this phase
-            for (int i = threadIdx.x; i < s.nwon; i += blockDim.x) ks[won[i]] += 1;
+            for (int i = threadIdx.x; i < s.nwon; i += blockDim.x) ks[won[i]] += (CB)1;
             cur ^= 1;
             __syncthreads();
         }
@@ -558,7 +576,7 @@ pr_status make_plan(int P, const int32_t *n_host, double eps, Plan &pl) {
         if (n < 1 || n > kMaxN) return fail(PR_ERR_INVALID, "batched: problem %d has n = %d (need 1..%d)", i, n, kMaxN);
         BDesc &d = pl.desc[i];
         d.n = n;
-        d.ldq = (n + 7) & ~7;
+        d.ldq = (n + 15) & ~15;  // rows start on 16 bytes in either storage type
         d.cb_off = cb;
         d.c_off = c;
         d.g_off = g;
@@ -623,7 +641,8 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     BDesc *d_desc = (BDesc *)(w + L.desc);
     int *d_order = (int *)(w + L.order);
     unsigned *d_max = (unsigned *)(w + L.maxbits);
-    uint16_t *d_cb = (uint16_t *)(w + L.cb);
+    void *d_cb = w + L.cb;
+    const bool cb8 = floor(1.0 / eps) <= (double)kMaxCbarByte;
     const DeviceInfo &di = device_info();
 
     k_binit<<<(P + 255) / 256, 256, 0, st>>>(ctl, d_max, P);
@@ -639,24 +658,40 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     if (src.points) {
         k_bpoints_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups, d_max);
         PR_CUDA(cudaGetLastError());
-        k_bpoints_quant<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups,
-                                               d_max, e, d_cb);
+        if (cb8)
+            k_bpoints_quant<uint8_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P,
+                                                            pl.groups, d_max, e, (uint8_t *)d_cb);
+        else
+            k_bpoints_quant<uint16_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P,
+                                                             pl.groups, d_max, e, (uint16_t *)d_cb);
     } else if (src.dt == PR_F64) {
-        k_bquant_matrix<double><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, e,
-                                                       d_cb, &ctl->head);
+        if (cb8)
+            k_bquant_matrix<double, uint8_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, e,
+                                                                    (uint8_t *)d_cb, &ctl->head);
+        else
+            k_bquant_matrix<double, uint16_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups,
+                                                                     e, (uint16_t *)d_cb, &ctl->head);
     } else {
-        k_bquant_matrix<float><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
-                                                      d_cb, &ctl->head);
+        if (cb8)
+            k_bquant_matrix<float, uint8_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
+                                                                   (uint8_t *)d_cb, &ctl->head);
+        else
+            k_bquant_matrix<float, uint16_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
+                                                                    (uint16_t *)d_cb, &ctl->head);
     }
     PR_CUDA(cudaGetLastError());
 
     const size_t smem = bsolve_smem(pl.n_max, pl.ldq_max, threads);
     if (smem > (size_t)di.max_smem_optin)
         return fail(PR_ERR_INVALID, "batched: problem of n = %d does not fit shared memory", pl.n_max);
-    const void *kern = threads == 128   ? (const void *)k_bsolve<128, 8>
-                       : threads == 256 ? (const void *)k_bsolve<256, 8>
-                       : threads == 512 ? (const void *)k_bsolve<512, 8>
-                                        : (const void *)k_bsolve<1024, 4>;
+    const void *kern = cb8 ? (threads == 128   ? (const void *)k_bsolve<128, 8, uint8_t>
+                              : threads == 256 ? (const void *)k_bsolve<256, 8, uint8_t>
+                              : threads == 512 ? (const void *)k_bsolve<512, 8, uint8_t>
+                                               : (const void *)k_bsolve<1024, 4, uint8_t>)
+                           : (threads == 128   ? (const void *)k_bsolve<128, 8, uint16_t>
+                              : threads == 256 ? (const void *)k_bsolve<256, 8, uint16_t>
+                              : threads == 512 ? (const void *)k_bsolve<512, 8, uint16_t>
+                                               : (const void *)k_bsolve<1024, 4, uint16_t>);
     PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -706,6 +741,8 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
         stats->rows_scanned = (int64_t)h.rows;
         stats->free_at_stop = 0;
         stats->threshold = 0;
+        stats->loop_ctas = 0;
+        stats->loop_cluster = 0;
         if (h.head.err != 0)
             return fail((pr_status)h.head.err, "batched: device reported %s", pr_status_string((pr_status)h.head.err));
     }

@@ -845,6 +845,8 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         stats->rows_scanned = 0;
         stats->free_at_stop = (int32_t)free_at_stop;
         stats->threshold = (int32_t)T;
+        stats->loop_ctas = 0;
+        stats->loop_cluster = 0;
     }
     if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
     return PR_OK;

@@ -20,9 +20,12 @@ __device__ __forceinline__ uint32_t quantise_elem(const float *row, int a, const
     return quantise_fbits(__float_as_uint(row[a]), e);
 }
 
-template <class T, bool VEC>
+// CB is the stored type: uint16_t, or uint8_t when every cbar <= 254 (the
+// caller checks floor(1/eps) <= 254); padding columns get 0x7FFF / 0xFF.
+template <class T, bool VEC, class CB>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
-                           EpsSplit e, uint16_t *__restrict__ cb, WsHead *head) {
+                           EpsSplit e, CB *__restrict__ cb, WsHead *head) {
+    constexpr uint32_t kPad = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
     // Grid-stride over (row, group of 8 columns); the row and group indices
     // advance by the stride's quotient and remainder (no division per step).
     const int groups = ldq >> 3;
@@ -64,7 +67,7 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                h[j] = a0 + j < nA ? quantise_elem(row, a0 + j, e) : (uint32_t)kPadCost;
+                h[j] = a0 + j < nA ? quantise_elem(row, a0 + j, e) : kPad;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -73,20 +76,26 @@ __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int n
                 h[j] = 0;
             }
         }
-        *reinterpret_cast<uint4 *>(cb + (long long)b * ldq + a0) =
-            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        if (sizeof(CB) == 1) {
+            *reinterpret_cast<uint2 *>(cb + (long long)b * ldq + a0) =
+                make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
+                           h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
+        } else {
+            *reinterpret_cast<uint4 *>(cb + (long long)b * ldq + a0) =
+                make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
     }
     if (bad) record_error(head, PR_ERR_INVALID);
 }
 
 // Launch k_quantise with 16-byte loads when every row starts 16-byte aligned.
-template <class T>
-void launch_quantise(const T *C, long long ldc, int nB, int nA, int ldq, double eps, uint16_t *cb,
+template <class T, class CB = uint16_t>
+void launch_quantise(const T *C, long long ldc, int nB, int nA, int ldq, double eps, CB *cb,
                      WsHead *head, int grid, cudaStream_t st) {
     const EpsSplit e = make_eps_split(eps);
     const bool vec = ((uintptr_t)C % 16 == 0) && ((ldc * (long long)sizeof(T)) % 16 == 0);
-    if (vec) k_quantise<T, true><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
-    else k_quantise<T, false><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
+    if (vec) k_quantise<T, true, CB><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
+    else k_quantise<T, false, CB><<<grid, 256, 0, st>>>(C, ldc, nB, nA, ldq, e, cb, head);
 }
 
 }  // namespace

@@ -121,6 +121,17 @@ __device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
     return m;
 }
 
+// Byte form of the test: bit j of the result is set iff byte j of
+// sat(c + k) equals the target (t4 = target in all four bytes), for the
+// sixteen bytes of one 16-byte load.
+__device__ __forceinline__ unsigned byte_bits(uint32_t w) {  // bit i = low bit of byte i
+    return ((w & 0x01010101u) * 0x01020408u) >> 24;
+}
+__device__ __forceinline__ unsigned eq_mask8(uint4 c, uint4 k, uint32_t t4) {
+    return byte_bits(__vcmpeq4(__vaddus4(c.x, k.x), t4)) | (byte_bits(__vcmpeq4(__vaddus4(c.y, k.y), t4)) << 4) |
+           (byte_bits(__vcmpeq4(__vaddus4(c.z, k.z), t4)) << 8) | (byte_bits(__vcmpeq4(__vaddus4(c.w, k.w), t4)) << 12);
+}
+
 // Read-only 16-byte load that does not allocate in L1 (streamed rows).
 __device__ __forceinline__ uint4 ld_nc_na_v4(const void *p) {
     uint4 v;

@@ -154,6 +154,29 @@ def test_full_size_n10000_more_seeds(prot, seed):
     dual_certificate(C, 0.01, got)
 
 
+@pytest.mark.parametrize("mode", ["grid", "cluster"])
+@pytest.mark.parametrize("n,eps", [(64, 0.1), (1000, 0.01), (4097, 0.005), (5003, 0.1)])
+def test_both_phase_loop_forms(prot, monkeypatch, mode, n, eps):
+    """The phase loop on the whole grid (barriers through L2) and in one
+    thread-block cluster (barriers through distributed shared memory) give
+    the same bit-exact result."""
+    monkeypatch.setenv("PR_PHASE_MODE", mode)
+    C = W.assignment_euclid_2d(n, 41 + n)
+    got = gpu_solve(prot, C, eps)
+    assert_parity(got, oracle.assign(C, eps))
+    assert got["stats"]["loop_cluster"] == (1 if mode == "cluster" else 0)
+    assert got["stats"]["loop_ctas"] >= (8 if mode == "cluster" else 100)
+
+
+@pytest.mark.parametrize("mode", ["grid", "cluster"])
+def test_full_size_n10000_both_forms(prot, monkeypatch, mode):
+    monkeypatch.setenv("PR_PHASE_MODE", mode)
+    C = W.assignment_euclid_2d(10000, 0)
+    got = gpu_solve(prot, C, 0.01)
+    assert_parity(got, oracle.assign(C, 0.01))
+    assert got["stats"]["loop_cluster"] == (1 if mode == "cluster" else 0)
+
+
 def test_repeat_is_deterministic(prot):
     C = W.assignment_euclid_2d(3000, 21)
     a = gpu_solve(prot, C, 0.01)
@@ -210,11 +233,13 @@ def test_bad_arguments(prot):
     assert b"ldc" in L.pr_last_error()
 
 
-def test_barrier_timeout_reported_not_hung(prot, monkeypatch):
+@pytest.mark.parametrize("mode", ["grid", "cluster"])
+def test_barrier_timeout_reported_not_hung(prot, monkeypatch, mode):
     """A one-cycle spin budget makes every waiting CTA give up at its first
-    grid barrier: the call returns PR_ERR_TIMEOUT and the context stays
-    usable (the next solve is exact)."""
+    barrier (grid or cluster form): the call returns PR_ERR_TIMEOUT and the
+    context stays usable (the next solve is exact)."""
     import torch
+    monkeypatch.setenv("PR_PHASE_MODE", mode)
     C = W.assignment_euclid_2d(2000, 2)
     monkeypatch.setenv("PR_SPIN_LIMIT_CYCLES", "1")
     with pytest.raises(prot.PrError) as e:
