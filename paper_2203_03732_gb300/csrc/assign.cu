@@ -460,7 +460,7 @@ constexpr long long kCopyWaitCycles = 2000000000ll;
 // with warps_per_row warps per row; cluster form: one row per warp through
 // its slot); then every proposal (atomicMax) or relabel at once; then the
 // pool donations.
-template <class CB, bool CL>
+template <class CB, bool SL>
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
@@ -469,12 +469,15 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
     const unsigned long long tA = p.profile ? gtimer() : 0;
-    // cluster form: every unknown y(b) is read here (the grid form reads it
-    // inside the row scan)
-    if (CL)
+    // More jobs than one register group holds go through the shared-memory
+    // slots (up to 16 rows in flight instead of rows_per_group); the choice is
+    // this CTA's own.  The slot scan reads every unknown y(b) first (the
+    // register scan reads it inside the row scan).
+    const bool via_slots = SL && nq > rows_per_group;
+    if (via_slots)
         for (int j = threadIdx.x; j < nq; j += blockDim.x)
             if (s.job_tgt[j] < 0) s.job_tgt[j] = ld_relaxed_s32(p.y_b + s.job_b[j]) - 1;
-    if (CL) {
+    if (via_slots) {
         // warp w scans jobs w, w + nslots, ... through its own slot
         __syncthreads();
         unsigned long long my_bytes = 0;
@@ -624,7 +627,11 @@ __host__ __device__ inline size_t slots_offset(int ldq, int key_bytes) {
     return (smem_bytes(ldq, key_bytes) + 127) & ~size_t(127);
 }
 
-template <class CB, bool CL>
+// CL: the launch is one thread-block cluster (barriers through distributed
+// shared memory) instead of a cooperative grid.  SL: a CTA whose jobs exceed
+// one register group scans them from per-warp shared-memory slots filled by
+// bulk copies (always with CL).
+template <class CB, bool CL, bool SL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -670,7 +677,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         s.bytes = s.rows = 0;
         s.err = 0;
         for (int i = 0; i < 4; ++i) s.cbar[i][0] = s.cbar[i][1] = 0;
-        if (CL) {
+        if (SL) {
             for (int w = 0; w < p.nslots; ++w)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s.mbar[w])) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -792,7 +799,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 }
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += gtimer() - t_mark;
-                run_jobs<CB, CL>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
+                run_jobs<CB, SL>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
                                  &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate);
                 if (p.profile) t_mark = gtimer();
             }
@@ -864,13 +871,13 @@ done:
             ctl->rounds = rounds;
         }
     }
+    // A copy whose wait gave up gets one more bounded wait: the CTA must not
+    // exit while it may still write the slot.
+    if (SL && (mstate & 2u)) mbar_wait(&s.mbar[threadIdx.x >> 5], mstate & 1u, kCopyWaitCycles);
     // Cluster mode: a CTA's shared memory must outlive every add another CTA
     // makes to it.  Every CTA gets here: the loop ends on the same shared
     // decision everywhere, or on a bounded wait that gave up.
     if (CL) {
-        // a copy whose wait gave up gets one more bounded wait: the CTA must
-        // not exit while it may still write the slot
-        if (mstate & 2u) mbar_wait(&s.mbar[threadIdx.x >> 5], mstate & 1u, kCopyWaitCycles);
         __syncthreads();
         cluster_barrier_hw();
     }
@@ -972,14 +979,14 @@ struct PhaseCfg {
     size_t smem = 0;
 };
 
-template <class CB, bool CL>
+template <class CB, bool CL, bool SL>
 pr_status set_phase_attrs(size_t smem) {
-    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return PR_OK;
 }
 
-// Largest cluster (16, else 8) of k_phases<CB, true> the device can hold, or 0.
+// Largest cluster (16, else 8) of k_phases<CB, true, true> the device can hold, or 0.
 template <class CB>
 int max_phase_cluster(size_t smem) {
     for (int cs : {16, 8}) {
@@ -995,7 +1002,7 @@ int max_phase_cluster(size_t smem) {
         c.attrs = at;
         c.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true>, &c) == cudaSuccess && n >= 1)
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true, true>, &c) == cudaSuccess && n >= 1)
             return cs;
         cudaGetLastError();  // clear a refusal of this size
     }
@@ -1015,14 +1022,16 @@ pr_status phase_cfg(PhaseCfg &cfg) {
     }
     const DeviceInfo &di = device_info();
     const size_t smem = (size_t)di.max_smem_optin;  // Smem + the key copy; see smem_bytes()
-    pr_status rc = set_phase_attrs<uint8_t, false>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true>(smem);
+    pr_status rc = set_phase_attrs<uint8_t, false, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true, true>(smem);
     if (rc != PR_OK) return rc;
     int per_sm = 0, per_sm16 = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false>, kThreads, smem));
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false, false>, kThreads, smem));
     if (per_sm16 < per_sm) per_sm = per_sm16;
     if (per_sm < 1) return fail(PR_ERR_INVALID, "phase kernel does not fit on an SM");
     int grid = di.sms * per_sm;
@@ -1055,6 +1064,17 @@ bool use_cluster(const PhaseCfg &cfg, int nslots, int n_rows) {
     if (m && strcmp(m, "grid") == 0) return false;
     if (m && strcmp(m, "cluster") == 0) return true;
     return n_rows <= kClusterMaxRows;
+}
+
+// Row scans of the grid form: a CTA with more jobs than one register group
+// sends them through shared-memory slots (measured at n = 10,000: eps = 0.1,
+// about 30 rows per CTA per round, 1.00 ms instead of 2.33 ms for the phase
+// loop; at eps = 0.01 the rounds hold 4 or 5 rows and stay on registers).
+// PR_SCAN=regs keeps every scan on registers.
+bool use_slots_in_grid(int nslots) {
+    if (nslots < kMinSlots) return false;
+    const char *m = getenv("PR_SCAN");
+    return !(m && strcmp(m, "regs") == 0);
 }
 
 // Everything after the argument checks, shared by pr_assign and
@@ -1122,13 +1142,16 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
         c.stream = st;
         c.attrs = at;
         c.numAttrs = 1;
-        if (cb8) PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint8_t, true>, p, warps_per_row, rows_per_group));
-        else PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint16_t, true>, p, warps_per_row, rows_per_group));
+        if (cb8) PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint8_t, true, true>, p, warps_per_row, rows_per_group));
+        else PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint16_t, true, true>, p, warps_per_row, rows_per_group));
     } else {
         Params pc = p;
         void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
-        const void *fn = cb8 ? (const void *)k_phases<uint8_t, false> : (const void *)k_phases<uint16_t, false>;
-        PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, smem_bytes(p.ldq, kb), st));
+        const bool sl = use_slots_in_grid(p.nslots);
+        const void *fn = sl ? (cb8 ? (const void *)k_phases<uint8_t, false, true> : (const void *)k_phases<uint16_t, false, true>)
+                            : (cb8 ? (const void *)k_phases<uint8_t, false, false> : (const void *)k_phases<uint16_t, false, false>);
+        const size_t smem = sl ? slots_offset(p.ldq, kb) + (size_t)p.nslots * p.slot_bytes : smem_bytes(p.ldq, kb);
+        PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, smem, st));
     }
     if (ev0 && ev1) PR_CUDA(cudaEventRecord(ev1, st));
 

@@ -154,27 +154,36 @@ def test_full_size_n10000_more_seeds(prot, seed):
     dual_certificate(C, 0.01, got)
 
 
-@pytest.mark.parametrize("mode", ["grid", "cluster"])
-@pytest.mark.parametrize("n,eps", [(64, 0.1), (1000, 0.01), (4097, 0.005), (5003, 0.1)])
-def test_both_phase_loop_forms(prot, monkeypatch, mode, n, eps):
-    """The phase loop on the whole grid (barriers through L2) and in one
+FORMS = ["grid", "grid-slots", "cluster"]
+
+
+def set_form(monkeypatch, form):
+    monkeypatch.setenv("PR_PHASE_MODE", "cluster" if form == "cluster" else "grid")
+    monkeypatch.setenv("PR_SCAN", "auto" if form == "grid-slots" else "regs")
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n,eps", [(64, 0.1), (1000, 0.01), (4097, 0.005), (5003, 0.1), (700, 0.002)])
+def test_all_phase_loop_forms(prot, monkeypatch, form, n, eps):
+    """The phase loop on the whole grid (barriers through L2; rows scanned
+    from registers or from bulk-copied shared-memory slots) and in one
     thread-block cluster (barriers through distributed shared memory) give
-    the same bit-exact result."""
-    monkeypatch.setenv("PR_PHASE_MODE", mode)
+    the same bit-exact result, in byte and in 16-bit storage."""
+    set_form(monkeypatch, form)
     C = W.assignment_euclid_2d(n, 41 + n)
     got = gpu_solve(prot, C, eps)
     assert_parity(got, oracle.assign(C, eps))
-    assert got["stats"]["loop_cluster"] == (1 if mode == "cluster" else 0)
-    assert got["stats"]["loop_ctas"] >= (8 if mode == "cluster" else 100)
+    assert got["stats"]["loop_cluster"] == (1 if form == "cluster" else 0)
+    assert got["stats"]["loop_ctas"] >= (8 if form == "cluster" else 100)
 
 
-@pytest.mark.parametrize("mode", ["grid", "cluster"])
-def test_full_size_n10000_both_forms(prot, monkeypatch, mode):
-    monkeypatch.setenv("PR_PHASE_MODE", mode)
+@pytest.mark.parametrize("form", FORMS)
+def test_full_size_n10000_all_forms(prot, monkeypatch, form):
+    set_form(monkeypatch, form)
     C = W.assignment_euclid_2d(10000, 0)
     got = gpu_solve(prot, C, 0.01)
     assert_parity(got, oracle.assign(C, 0.01))
-    assert got["stats"]["loop_cluster"] == (1 if mode == "cluster" else 0)
+    assert got["stats"]["loop_cluster"] == (1 if form == "cluster" else 0)
 
 
 def test_repeat_is_deterministic(prot):
@@ -233,13 +242,13 @@ def test_bad_arguments(prot):
     assert b"ldc" in L.pr_last_error()
 
 
-@pytest.mark.parametrize("mode", ["grid", "cluster"])
-def test_barrier_timeout_reported_not_hung(prot, monkeypatch, mode):
+@pytest.mark.parametrize("form", FORMS)
+def test_barrier_timeout_reported_not_hung(prot, monkeypatch, form):
     """A one-cycle spin budget makes every waiting CTA give up at its first
     barrier (grid or cluster form): the call returns PR_ERR_TIMEOUT and the
     context stays usable (the next solve is exact)."""
     import torch
-    monkeypatch.setenv("PR_PHASE_MODE", mode)
+    set_form(monkeypatch, form)
     C = W.assignment_euclid_2d(2000, 2)
     monkeypatch.setenv("PR_SPIN_LIMIT_CYCLES", "1")
     with pytest.raises(prot.PrError) as e:
