@@ -18,18 +18,19 @@
 // or it held a's free copies) the planes swap roles: the emptied plane is
 // all zero and becomes the new "hi" plane.
 //
-// One phase (B' = supply vertices with free copies), steps as kernels:
-//   k_ot_phase_start  r_b = f_b, flags, the free-copy total for the stop test
-//   round R: k_ot_propose  every searching b proposes (atomicMax on the
-//                          column word) to the lowest admissible a >= its
-//                          resume column with unmatched lo copies left;
-//            k_ot_grant    a's lowest proposer b gets g = min(r_b, avail_a)
-//                          copies; partners of matched lo copies are evicted,
-//                          highest supply index first (step II)
-//   k_ot_phase_end    F_b += 1 for b in B' left with unplaced copies (III b);
-//                     clusters shift up where the lo cluster is empty (III a)
-// The host runs the loop and reads one counter per round and per phase, so
-// pr_ot synchronises its stream.
+// One phase (B' = supply vertices with free copies), steps of k_ot_loop (one
+// cooperative launch; a grid barrier with a summed payload after each step):
+//   ot_phase_start  r_b = f_b, flags, the free-copy total for the stop test
+//   round R: ot_propose  every searching b proposes (atomicMax on the column
+//                        word) to the lowest admissible a >= its resume
+//                        column with unmatched lo copies left;
+//            ot_grant    a's lowest proposer b gets g = min(r_b, avail_a)
+//                        copies; partners of matched lo copies are evicted,
+//                        highest supply index first (step II)
+//   ot_phase_end    F_b += 1 for b in B' left with unplaced copies (III b);
+//                   clusters shift up where the lo cluster is empty (III a)
+// The host reads the counters once, after the loop (the plan size check
+// then synchronises the stream).
 //
 // Plan and fix-up (a reading: the paper defers this part to another paper):
 // mass(b,a) = matched copies / theta; a demand that received more than mu_a
@@ -60,11 +61,12 @@ constexpr int kFlagSearching = 1, kFlagInBp = 2;
 
 struct OCtl {
     WsHead head;
-    unsigned long long nfree;  // free supply copies at the phase start
-    int nprop;                 // proposals of the current round
-    int nnz;                   // plan entries from the matched copies
-    int n_nw;                  // north-west corner allocations
-    int n_extra;               // allocations on pairs without matched copies
+    unsigned long long bar[4];  // payload barrier slots of k_ot_loop
+    long long phases, rounds, free_at_stop, threshold;
+    int nnz;                    // plan entries from the matched copies
+    int n_nw;                   // north-west corner allocations
+    int n_extra;                // allocations on pairs without matched copies
+    int pad;
     long long bytes;
 };
 
@@ -188,10 +190,19 @@ __global__ void k_ot_ctl_init(OCtl *c) {
     c->head.magic = kWsMagic;
 }
 
-__global__ void k_ot_phase_start(OParams p) {
-    __shared__ unsigned long long part;
-    if (threadIdx.x == 0) part = 0;
+// Sum over the CTA of one value per thread (every thread gets the sum).
+__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v) {
+    __shared__ unsigned long long acc;
     __syncthreads();
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    if (v) atomicAdd(&acc, v);
+    __syncthreads();
+    return acc;
+}
+
+// Phase start: r_b = f_b, B' = {b : f_b > 0}; returns this thread's free copies.
+__device__ __forceinline__ unsigned long long ot_phase_start(const OParams &p) {
     unsigned long long mine = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x) {
         const int fb = p.f[b];
@@ -201,21 +212,14 @@ __global__ void k_ot_phase_start(OParams p) {
         p.pa[b] = -1;
         mine += (unsigned long long)fb;
     }
-    atomicAdd(&part, mine);
-    __syncthreads();
-    if (threadIdx.x == 0 && part) atomicAdd(&p.ctl->nfree, part);
+    return mine;
 }
 
 // Warp per searching supply vertex: the lowest a >= ptr with
 // cbar + kmin_a == F_b - 1 and avail_a > 0.
-__global__ void __launch_bounds__(kOtThreads) k_ot_propose(OParams p, unsigned R) {
-    __shared__ int props;
-    __shared__ unsigned long long sbytes;
-    if (threadIdx.x == 0) {
-        props = 0;
-        sbytes = 0;
-    }
-    __syncthreads();
+// Returns this thread's proposals (lane 0 of each warp counts its rows).
+__device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, unsigned long long &bytes_out) {
+    unsigned props = 0;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -264,27 +268,22 @@ __global__ void __launch_bounds__(kOtThreads) k_ot_propose(OParams p, unsigned R
                 atomicMax(p.prop + found, word_of(R, b));
                 p.pa[b] = found;
                 p.ptr[b] = found;
-                atomicAdd(&props, 1);
+                ++props;
             } else {
                 p.flag[b] &= ~kFlagSearching;
             }
         }
     }
-    if (lane == 0 && bytes) atomicAdd(&sbytes, bytes);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (props) atomicAdd(&p.ctl->nprop, props);
-        if (sbytes) atomicAdd((unsigned long long *)&p.ctl->bytes, sbytes);
-    }
+    if (lane == 0) bytes_out += bytes;
+    return props;
 }
 
 // Warp per proposer: the winner of a takes g copies; the partners of matched
 // lo copies are evicted from the highest supply index down.
-__global__ void __launch_bounds__(kOtThreads) k_ot_grant(OParams p) {
+__device__ __forceinline__ void ot_grant(const OParams &p) {
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->nprop = 0;  // read by the host already
     for (int b = warp_g; b < p.nB; b += nwarps) {
         const int a = p.pa[b];
         if (a < 0) continue;
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(kOtThreads) k_ot_grant(OParams p) {
     }
 }
 
-__global__ void k_ot_phase_end(OParams p) {
+__device__ __forceinline__ void ot_phase_end(const OParams &p) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (int b = t0; b < p.nB; b += stride)
@@ -351,7 +350,65 @@ __global__ void k_ot_phase_end(OParams p) {
         }
         p.avail[a] = p.clo[a];
     }
-    if (t0 == 0) p.ctl->nfree = 0;
+}
+
+// Every phase and round of Sec. 4's cluster form in one cooperative launch;
+// grid barriers with summed payloads stand between the steps, so the host
+// reads nothing until the loop is over.  The stop rule is Sec. 3.3 on the
+// copy instance: T = floor(eps * S), S the total supply copies, the phase cap
+// S (2K + 3) / (T + 1) + 1 with K = floor(1/eps).
+__global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps, long long spin_limit) {
+    OCtl *c = p.ctl;
+    // invalid masses or costs (recorded by the earlier kernels of the solve):
+    // the copy counts are not all written, so no loop runs (every CTA reads
+    // the same value)
+    if (ld_relaxed_s32(&c->head.err) != 0) return;
+    const unsigned G = gridDim.x;
+    unsigned gen = 0;
+    unsigned long long sum = 0;
+    unsigned long long s_loc = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x)
+        s_loc += (unsigned long long)p.S[b];
+    s_loc = cta_sum(s_loc);
+    if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, s_loc, sum)) return;
+    const long long S_total = (long long)sum;
+    const long long T = (long long)floor(eps * (double)S_total);
+    const long long K = (long long)floor(1.0 / eps);
+    const long long cap = (S_total * (2 * K + 3)) / (T + 1) + 1;
+    long long phases = 0, rounds = 0;
+    unsigned R = 0;
+    unsigned long long bytes = 0;
+    for (;;) {
+        const unsigned long long nf = cta_sum(ot_phase_start(p));
+        if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, nf, sum)) return;
+        const long long nfree = (long long)sum;
+        if (nfree <= T || phases >= cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                c->free_at_stop = nfree;
+                c->threshold = T;
+                if (nfree > T) record_error(&c->head, PR_ERR_NO_CONVERGENCE);
+            }
+            break;
+        }
+        ++phases;
+        for (;;) {
+            ++R;
+            const unsigned long long np = cta_sum(ot_propose(p, R, bytes));
+            if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, np, sum)) return;
+            if (sum == 0) break;
+            ++rounds;
+            ot_grant(p);
+            if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, 0, sum)) return;
+        }
+        ot_phase_end(p);
+        if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, 0, sum)) return;
+    }
+    const unsigned long long cb = cta_sum(bytes);
+    if (threadIdx.x == 0 && cb) atomicAdd((unsigned long long *)&c->bytes, cb);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->phases = phases;
+        c->rounds = rounds;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -533,23 +590,37 @@ __global__ void k_fix_nw(FixParams fp, int use_smem, OCtl *ctl) {
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    // The walk is one chain of FP64 subtractions, so it runs in one thread.
+    // The two current residuals live in registers; the next entry is read only
+    // when one is used up.  Each step's t is the smaller residual, which
+    // therefore becomes exactly 0, so only the other one is subtracted.  The
+    // residuals are never negative, so every comparison is made on the bit
+    // patterns as integers (same order as the doubles; <= 0 also covers -0.0
+    // and any negative value), leaving one FP64 operation per step.
     int i = 0, j = 0, n = 0;
+    long long r = p.nB > 0 ? __double_as_longlong(rr[0]) : 0, q = p.nA > 0 ? __double_as_longlong(qq[0]) : 0;
     while (i < p.nB && j < p.nA) {
-        if (rr[i] <= 0.0) {
-            ++i;
+        if (r <= 0) {
+            if (++i < p.nB) r = __double_as_longlong(rr[i]);
             continue;
         }
-        if (qq[j] <= 0.0) {
-            ++j;
+        if (q <= 0) {
+            if (++j < p.nA) q = __double_as_longlong(qq[j]);
             continue;
         }
-        const double t = rr[i] < qq[j] ? rr[i] : qq[j];
+        const bool rs = r < q;  // the supply residual is the smaller
+        const long long t = rs ? r : q;
         fp.nw_b[n] = i;
         fp.nw_a[n] = j;
-        fp.nw_t[n] = t;
+        fp.nw_t[n] = __longlong_as_double(t);
         ++n;
-        rr[i] = __dsub_rn(rr[i], t);
-        qq[j] = __dsub_rn(qq[j], t);
+        if (rs) {
+            q = __double_as_longlong(__dsub_rn(__longlong_as_double(q), __longlong_as_double(t)));
+            r = 0;
+        } else {
+            r = __double_as_longlong(__dsub_rn(__longlong_as_double(r), __longlong_as_double(t)));
+            q = 0;
+        }
     }
     ctl->n_nw = n;
 }
@@ -716,56 +787,25 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
                                    &p.ctl->head, qgrid, st);
         PR_CUDA(cudaGetLastError());
     }
+    const int gw = di.sms * 8;  // warps-per-row kernels of the fix-up: grid of 256-thread CTAs
+    {
+        // the phase loop: one cooperative launch, as many CTAs as fit (at
+        // most 1023, the barrier's arrival field)
+        int per_sm = 0;
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ot_loop, kOtThreads, 0));
+        if (per_sm < 1) return fail(PR_ERR_INVALID, "pr_ot: loop kernel does not fit on an SM");
+        const int grid = std::min(di.sms * per_sm, 1023);
+        const long long limit = spin_limit_cycles();
+        void *args[] = {(void *)&p, (void *)&eps, (void *)&limit};
+        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_ot_loop, dim3(grid), dim3(kOtThreads), args, 0, st));
+    }
     OCtl h;
     PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
     PR_CUDA(cudaStreamSynchronize(st));
-    if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: invalid costs or masses");
-    // S = total supply copies; T = floor(eps * S) (Sec. 3.3 on the copy instance)
-    std::vector<int> hS(nB);
-    PR_CUDA(cudaMemcpyAsync(hS.data(), p.S, sizeof(int) * nB, cudaMemcpyDeviceToHost, st));
-    PR_CUDA(cudaStreamSynchronize(st));
-    long long S_total = 0;
-    for (int b = 0; b < nB; ++b) S_total += hS[b];
-    const long long T = (long long)floor(eps * (double)S_total);
-    const long long K = (long long)floor(1.0 / eps);
-    const long long cap = (S_total * (2 * K + 3)) / (T + 1) + 1;
-
-    const int gw = di.sms * 8;  // warps-per-row kernels: grid of 256-thread CTAs
-    long long phases = 0, rounds = 0;
-    unsigned R = 0;
-    long long free_at_stop = 0;
+    if (h.head.err == PR_ERR_INVALID) return fail(PR_ERR_INVALID, "pr_ot: invalid costs or masses");
+    if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
+    const long long phases = h.phases, rounds = h.rounds, free_at_stop = h.free_at_stop, T = h.threshold;
     pr_status rc = PR_OK;
-    for (;;) {
-        k_ot_phase_start<<<g1, 256, 0, st>>>(p);
-        PR_CUDA(cudaGetLastError());
-        unsigned long long nfree = 0;
-        PR_CUDA(cudaMemcpyAsync(&nfree, &p.ctl->nfree, sizeof(nfree), cudaMemcpyDeviceToHost, st));
-        PR_CUDA(cudaStreamSynchronize(st));
-        if ((long long)nfree <= T) {
-            free_at_stop = (long long)nfree;
-            break;
-        }
-        if (phases >= cap) {
-            free_at_stop = (long long)nfree;
-            rc = fail(PR_ERR_NO_CONVERGENCE, "pr_ot: phase cap reached");
-            break;
-        }
-        ++phases;
-        for (;;) {
-            ++R;
-            k_ot_propose<<<gw, kOtThreads, 0, st>>>(p, R);
-            PR_CUDA(cudaGetLastError());
-            int nprop = 0;
-            PR_CUDA(cudaMemcpyAsync(&nprop, &p.ctl->nprop, sizeof(int), cudaMemcpyDeviceToHost, st));
-            PR_CUDA(cudaStreamSynchronize(st));
-            if (nprop == 0) break;
-            ++rounds;
-            k_ot_grant<<<gw, kOtThreads, 0, st>>>(p);
-            PR_CUDA(cudaGetLastError());
-        }
-        k_ot_phase_end<<<g1, 256, 0, st>>>(p);
-        PR_CUDA(cudaGetLastError());
-    }
     if (rc != PR_OK) return rc;
 
     // plan and fix-up

@@ -143,4 +143,48 @@ __device__ __forceinline__ bool grid_barrier(WsHead *h, unsigned &gen, unsigned 
     return s_abort == 0;
 }
 
+// Grid barrier that also sums one value per CTA, rotating over four 64-bit
+// slots: barrier h adds (1 | v << 10) to slot h % 4 with a release
+// reduction, then polls it (acquire, bounded by `limit` clock64 cycles) until
+// the arrival field (bits 0..9, at most 1023 CTAs) reaches the grid size.
+// CTA 0 zeroes slot (h + 2) % 4 during barrier h: every CTA read it at
+// barrier h - 2, and barrier h + 2 can start only after barrier h + 1, which
+// needs CTA 0's arrival.  `sum` receives the sum of the v (54 bits); on
+// time-out or abort the call returns false and the kernel must stop.
+__device__ __forceinline__ bool grid_sum_barrier(unsigned long long *slots, WsHead *h, unsigned &gen,
+                                                 unsigned nblocks, long long limit, unsigned long long v,
+                                                 unsigned long long &sum) {
+    __shared__ unsigned long long s_pub;
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = gen + 1;
+        unsigned long long *slot = slots + (g & 3);
+        if (blockIdx.x == 0) slots[(g + 2) & 3] = 0;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(slot), "l"(1ull | (v << 10)) : "memory");
+        unsigned long long w = 0;
+        const long long t0 = clock64();
+        int ok = 1;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(slot) : "memory");
+            if ((w & 1023ull) == (unsigned long long)nblocks) break;
+            if (ld_relaxed_s32(&h->abort)) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > limit) {
+                record_error(h, PR_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        s_pub = w >> 10;
+        s_ok = ok;
+    }
+    __syncthreads();
+    gen += 1;
+    sum = s_pub;
+    return s_ok != 0;
+}
+
 }  // namespace prot

@@ -85,3 +85,28 @@ def test_ot_bad_masses(prot):
     nu[3] = -0.1
     with pytest.raises(prot.PrError):
         prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.1)
+
+
+def test_ot_barrier_timeout_reported_not_hung(prot, monkeypatch):
+    """The loop kernel's grid barriers wait at most PR_SPIN_LIMIT_CYCLES: with
+    one cycle every CTA gives up at its first barrier, pr_ot returns
+    PR_ERR_TIMEOUT and the next solve is exact."""
+    import torch
+    C, nu, mu = W.ot_euclid_2d(300, 257, 9)
+    monkeypatch.setenv("PR_SPIN_LIMIT_CYCLES", "1")
+    with pytest.raises(prot.PrError) as e:
+        prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.05)
+    assert e.value.status == -3
+    monkeypatch.delenv("PR_SPIN_LIMIT_CYCLES")
+    r, dense = gpu_ot(prot, C, nu, mu, 0.05)
+    assert_ot_parity(r, dense, O.ot(C, nu, mu, 0.05))
+
+
+@pytest.mark.parametrize("nB,nA,eps,seed", [(400, 300, 0.01, 5), (150, 600, 0.02, 6)])
+def test_ot_many_phases(prot, nB, nA, eps, seed):
+    """Small eps: many phases, cluster shifts and evictions in the loop kernel."""
+    C, nu, mu = W.ot_euclid_2d(nB, nA, seed)
+    r, dense = gpu_ot(prot, C, nu, mu, eps)
+    ref = O.ot(C, nu, mu, eps)
+    assert ref["stats"]["phases"] > 3
+    assert_ot_parity(r, dense, ref)
