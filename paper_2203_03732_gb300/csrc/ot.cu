@@ -58,6 +58,7 @@ constexpr int kOtThreads = 256;
 constexpr int kOtUnroll = 8;
 constexpr int kOtChunk = 32 * 8 * kOtUnroll;
 constexpr int kFlagSearching = 1, kFlagInBp = 2;
+constexpr int kFixUnroll = 8;  // plan-column chunks of 32 counts read at a time
 
 struct OCtl {
     WsHead head;
@@ -439,21 +440,29 @@ __global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
         const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
         int nnz = 0, last = -1;
         double recv = 0.0, before_last = 0.0, m_last = 0.0;
-        for (int b0 = 0; b0 < p.nB; b0 += 32) {
-            const int b = b0 + lane;
-            const int c = b < p.nB ? lo[b] + hi[b] : 0;
-            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
-            if (!nz) continue;
-            nnz += __popc(nz);
-            const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
-            // lane order = ascending b: fold the chunk's masses in that order
-            for (unsigned w = nz; w; w &= w - 1) {
-                const int L = __ffs(w) - 1;
-                const double mi = __shfl_sync(0xFFFFFFFFu, m, L);
-                before_last = recv;
-                m_last = mi;
-                recv = __dadd_rn(recv, mi);
-                last = b0 + L;
+        for (int g0 = 0; g0 < p.nB; g0 += 32 * kFixUnroll) {
+            int cs[kFixUnroll];  // kFixUnroll chunks of 32 counts in flight
+#pragma unroll
+            for (int u = 0; u < kFixUnroll; ++u) {
+                const int b = g0 + 32 * u + lane;
+                cs[u] = b < p.nB ? lo[b] + hi[b] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kFixUnroll; ++u) {
+                const int b0 = g0 + 32 * u, c = cs[u];
+                const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+                if (!nz) continue;
+                nnz += __popc(nz);
+                const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
+                // lane order = ascending b: fold the chunk's masses in that order
+                for (unsigned w = nz; w; w &= w - 1) {
+                    const int L = __ffs(w) - 1;
+                    const double mi = __shfl_sync(0xFFFFFFFFu, m, L);
+                    before_last = recv;
+                    m_last = mi;
+                    recv = __dadd_rn(recv, mi);
+                    last = b0 + L;
+                }
             }
         }
         if (lane == 0) {
@@ -524,23 +533,31 @@ __global__ void __launch_bounds__(kOtThreads) k_fix_write(FixParams fp) {
         const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
         int pos = fp.off_a[a];
         const int tb = fp.trim_b[a];
-        for (int b0 = 0; b0 < p.nB; b0 += 32) {
-            const int b = b0 + lane;
-            const int c = b < p.nB ? lo[b] + hi[b] : 0;
-            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
-            if (!nz) continue;
-            if (c) {
-                const int k = pos + __popc(nz & ((1u << lane) - 1));
-                double m = __ddiv_rn((double)c, fp.theta);
-                if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
-                if (k < fp.plan_cap) {
-                    fp.plan_row[k] = b;
-                    fp.plan_col[k] = a;
-                    fp.plan_mass[k] = m;
-                }
-                atomicAdd(fp.cnt_b + b, 1);
+        for (int g0 = 0; g0 < p.nB; g0 += 32 * kFixUnroll) {
+            int cs[kFixUnroll];
+#pragma unroll
+            for (int u = 0; u < kFixUnroll; ++u) {
+                const int b = g0 + 32 * u + lane;
+                cs[u] = b < p.nB ? lo[b] + hi[b] : 0;
             }
-            pos += __popc(nz);
+#pragma unroll
+            for (int u = 0; u < kFixUnroll; ++u) {
+                const int b = g0 + 32 * u + lane, c = cs[u];
+                const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+                if (!nz) continue;
+                if (c) {
+                    const int k = pos + __popc(nz & ((1u << lane) - 1));
+                    double m = __ddiv_rn((double)c, fp.theta);
+                    if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
+                    if (k < fp.plan_cap) {
+                        fp.plan_row[k] = b;
+                        fp.plan_col[k] = a;
+                        fp.plan_mass[k] = m;
+                    }
+                    atomicAdd(fp.cnt_b + b, 1);
+                }
+                pos += __popc(nz);
+            }
         }
     }
 }
