@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the eps sweep, batched, autograd and OT measurements")
+    ap.add_argument("--ot-once", action="store_true",
+                    help="only the OT workload: two warm solves, then --steps timed ones (profiling runs)")
     return ap.parse_args()
 
 
@@ -326,20 +328,25 @@ def run_extras(a, torch, prot, W, dev, stream):
                       "speedup_vs_plain": ms_ag_plain / ms_ag}
     del costs
 
-    # OT: 10k x 10k, Dirichlet(1) masses, Euclidean / max, eps 0.05
+    ex["ot"] = run_ot(a, torch, prot, W, dev, reps=3)
+    return ex
+
+
+def run_ot(a, torch, prot, W, dev, reps):
+    """OT: n x n, Dirichlet(1) masses, Euclidean / max, eps 0.05; one warm-up
+    solve, then `reps` timed ones (pr_ot synchronises: host clock)."""
     Co, nu, mu = W.ot_euclid_2d(a.n, a.n, 0)
     Cod, nud, mud = (torch.from_numpy(x).to(dev) for x in (Co, nu, mu))
     wso = prot.Workspace(dev)
-    r = prot.ot(Cod, nud, mud, 0.05, ws=wso)
+    for _ in range(2):
+        r = prot.ot(Cod, nud, mud, 0.05, ws=wso)
     t0 = time.perf_counter()
-    reps = 3
     for _ in range(reps):
         r = prot.ot(Cod, nud, mud, 0.05, ws=wso)
-    ms_ot = (time.perf_counter() - t0) * 1e3 / reps  # pr_ot synchronises: host clock
-    ex["ot"] = {"workload": "OT 10k x 10k, 2-D uniform, Euclidean / max, Dirichlet(1) masses, eps=0.05",
-                "ms": ms_ot, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
-                "plan_nnz": int(r["plan_row"].numel()), "cost": float(r["cost"].cpu())}
-    return ex
+    ms_ot = (time.perf_counter() - t0) * 1e3 / reps
+    return {"workload": f"OT {a.n} x {a.n}, 2-D uniform, Euclidean / max, Dirichlet(1) masses, eps=0.05",
+            "ms": ms_ot, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+            "plan_nnz": int(r["plan_row"].numel()), "cost": float(r["cost"].cpu())}
 
 
 def main():
@@ -358,6 +365,9 @@ def main():
     from paper_2203_03732_gb300 import workloads as W
 
     torch.cuda.set_device(local)
+    if a.ot_once:
+        print(json.dumps({"ot": run_ot(a, torch, prot, W, torch.device("cuda", local), reps=max(1, a.steps))}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
