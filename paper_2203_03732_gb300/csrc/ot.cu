@@ -82,7 +82,7 @@ struct OLayout {
 OLayout make_olayout(int nB, int nA) {
     OLayout L;
     Carver c;
-    L.ldq = (nA + 7) & ~7;
+    L.ldq = (nA + 15) & ~15;  // rows start on 16 bytes in either storage type
     L.ctl = c.take<OCtl>(1);
     L.cb = c.take<uint16_t>((size_t)nB * L.ldq);
     L.key = c.take<uint16_t>(L.ldq);
@@ -124,8 +124,8 @@ OLayout make_olayout(int nB, int nA) {
 
 struct OParams {
     OCtl *ctl;
-    const uint16_t *cb;
-    uint16_t *key;
+    const void *cb;  // uint8_t or uint16_t [nB][ldq] (bytes when floor(1/eps) <= 252)
+    void *key;       // k = kmin_a per column, in the same type (padding 0xFF / 0x8000)
     int *S, *D, *F, *f, *r, *ptr, *pa, *flag;
     int *kmin, *clo, *chi, *avail, *sel, *granted;
     unsigned long long *prop;
@@ -158,6 +158,7 @@ __global__ void k_ot_counts(const double *nu, const double *mu, int nB, int nA, 
     }
 }
 
+template <class CB>
 __global__ void k_ot_init(OParams p) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,7 +171,7 @@ __global__ void k_ot_init(OParams p) {
         p.flag[b] = 0;
     }
     for (int a = t0; a < p.ldq; a += stride) {
-        p.key[a] = a < p.nA ? 0 : kPadKey;
+        static_cast<CB *>(p.key)[a] = a < p.nA ? (CB)0 : (CB)(sizeof(CB) == 1 ? 0xFF : kPadKey);
         if (a >= p.nA) continue;
         p.kmin[a] = 0;
         p.clo[a] = p.D[a];
@@ -219,38 +220,42 @@ __device__ __forceinline__ unsigned long long ot_phase_start(const OParams &p) {
 // Warp per searching supply vertex: the lowest a >= ptr with
 // cbar + kmin_a == F_b - 1 and avail_a > 0.
 // Returns this thread's proposals (lane 0 of each warp counts its rows).
+template <class CB>
 __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, unsigned long long &bytes_out) {
+    constexpr int W = 16 / (int)sizeof(CB);  // columns per 16-byte load
+    constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
+    constexpr int kChunkW = 32 * W * kOtUnroll;
     unsigned props = 0;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const CB *key = static_cast<const CB *>(p.key);
     unsigned long long bytes = 0;
     for (int b = warp_g; b < p.nB; b += nwarps) {
         if (!(p.flag[b] & kFlagSearching)) continue;
         const uint32_t tgt = (uint32_t)(p.F[b] - 1);
-        const uint32_t t2 = tgt | (tgt << 16);
-        const uint16_t *row = p.cb + (size_t)b * p.ldq;
+        const uint32_t t2 = W == 8 ? (tgt | (tgt << 16)) : tgt * 0x01010101u;
+        const CB *row = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq;
         const int start = p.ptr[b];
         int found = -1;
-        for (int c0 = start & ~7; c0 < p.ldq && found < 0; c0 += kOtChunk) {
-            uint4 sv[kOtUnroll];
+        for (int c0 = start & ~(W - 1); c0 < p.ldq && found < 0; c0 += kChunkW) {
+            uint4 cv[kOtUnroll];
 #pragma unroll
             for (int u = 0; u < kOtUnroll; ++u) {
-                const int idx = c0 + u * 256 + lane * 8;
-                if (idx < p.ldq) {
-                    const uint4 c = ld_nc_na_v4(row + idx);
-                    const uint4 k = *reinterpret_cast<const uint4 *>(p.key + idx);
-                    sv[u] = make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
-                } else {
-                    sv[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-                }
+                const int idx = c0 + u * 32 * W + lane * W;
+                cv[u] = idx < p.ldq ? ld_nc_na_v4(row + idx) : make_uint4(0, 0, 0, 0);
             }
-            bytes += 2ull * (unsigned long long)min(kOtChunk, p.ldq - c0);
+            bytes += sizeof(CB) * (unsigned long long)min(kChunkW, p.ldq - c0);
             for (int u = 0; u < kOtUnroll && found < 0; ++u) {
-                const int idx = c0 + u * 256 + lane * 8;
-                unsigned m = eq_mask(sv[u], t2);
+                const int idx = c0 + u * 32 * W + lane * W;
+                unsigned m = 0;
+                if (idx < p.ldq) {
+                    const uint4 kv = *reinterpret_cast<const uint4 *>(key + idx);
+                    m = W == 8 ? eq_mask(make_uint4(cv[u].x + kv.x, cv[u].y + kv.y, cv[u].z + kv.z, cv[u].w + kv.w), t2)
+                               : eq_mask8(cv[u], kv, t2);
+                }
                 const int lo = start - idx;
-                if (lo > 0) m &= lo >= 8 ? 0u : (0xFFu << lo) & 0xFFu;
+                if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
                 for (;;) {
                     const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
                     if (any == 0) break;
@@ -333,6 +338,7 @@ __device__ __forceinline__ void ot_grant(const OParams &p) {
     }
 }
 
+template <class CB>
 __device__ __forceinline__ void ot_phase_end(const OParams &p) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,7 +350,7 @@ __device__ __forceinline__ void ot_phase_end(const OParams &p) {
         if (p.clo[a] == 0 && p.chi[a] > 0) {  // step (III a): clusters shift up
             const int k = p.kmin[a] + 1;
             p.kmin[a] = k;
-            p.key[a] = (uint16_t)k;
+            static_cast<CB *>(p.key)[a] = (CB)k;  // bytes: k <= floor(1/eps) + 2 <= 254
             p.clo[a] = p.chi[a];
             p.chi[a] = 0;
             p.sel[a] ^= 1;
@@ -358,6 +364,7 @@ __device__ __forceinline__ void ot_phase_end(const OParams &p) {
 // reads nothing until the loop is over.  The stop rule is Sec. 3.3 on the
 // copy instance: T = floor(eps * S), S the total supply copies, the phase cap
 // S (2K + 3) / (T + 1) + 1 with K = floor(1/eps).
+template <class CB>
 __global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps, long long spin_limit) {
     OCtl *c = p.ctl;
     // invalid masses or costs (recorded by the earlier kernels of the solve):
@@ -394,14 +401,14 @@ __global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps
         ++phases;
         for (;;) {
             ++R;
-            const unsigned long long np = cta_sum(ot_propose(p, R, bytes));
+            const unsigned long long np = cta_sum(ot_propose<CB>(p, R, bytes));
             if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, np, sum)) return;
             if (sum == 0) break;
             ++rounds;
             ot_grant(p);
             if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, 0, sum)) return;
         }
-        ot_phase_end(p);
+        ot_phase_end<CB>(p);
         if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, 0, sum)) return;
     }
     const unsigned long long cb = cta_sum(bytes);
@@ -761,8 +768,8 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
 
     OParams p;
     p.ctl = (OCtl *)(w + L.ctl);
-    p.cb = (const uint16_t *)(w + L.cb);
-    p.key = (uint16_t *)(w + L.key);
+    p.cb = w + L.cb;
+    p.key = w + L.key;
     p.S = (int *)(w + L.S);
     p.D = (int *)(w + L.D);
     p.F = (int *)(w + L.F);
@@ -790,31 +797,43 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     PR_CUDA(cudaGetLastError());
     k_ot_counts<<<g1, 256, 0, st>>>(supply, demand, nB, nA, theta, p.S, p.D, &p.ctl->head);
     PR_CUDA(cudaGetLastError());
-    k_ot_init<<<g1 * 4, 256, 0, st>>>(p);
+    // bytes for the rounded costs and keys when every cbar and key fits one
+    // (floor(1/eps) <= 252, as in pr_assign)
+    const bool cb8 = floor(1.0 / eps) <= 252.0;
+    if (cb8) k_ot_init<uint8_t><<<g1 * 4, 256, 0, st>>>(p);
+    else k_ot_init<uint16_t><<<g1 * 4, 256, 0, st>>>(p);
     PR_CUDA(cudaGetLastError());
     {
         const long long groups = (long long)nB * (L.ldq >> 3);
         const long long want = groups / 256 + 1;
         const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
-        if (dt == PR_F64)
-            launch_quantise<double>((const double *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)p.cb,
-                                    &p.ctl->head, qgrid, st);
+        void *cbw = const_cast<void *>(p.cb);
+        if (dt == PR_F64 && cb8)
+            launch_quantise<double, uint8_t>((const double *)C, ldc, nB, nA, L.ldq, eps, (uint8_t *)cbw,
+                                             &p.ctl->head, qgrid, st);
+        else if (dt == PR_F64)
+            launch_quantise<double, uint16_t>((const double *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)cbw,
+                                              &p.ctl->head, qgrid, st);
+        else if (cb8)
+            launch_quantise<float, uint8_t>((const float *)C, ldc, nB, nA, L.ldq, eps, (uint8_t *)cbw,
+                                            &p.ctl->head, qgrid, st);
         else
-            launch_quantise<float>((const float *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)p.cb,
-                                   &p.ctl->head, qgrid, st);
+            launch_quantise<float, uint16_t>((const float *)C, ldc, nB, nA, L.ldq, eps, (uint16_t *)cbw,
+                                             &p.ctl->head, qgrid, st);
         PR_CUDA(cudaGetLastError());
     }
     const int gw = di.sms * 8;  // warps-per-row kernels of the fix-up: grid of 256-thread CTAs
     {
         // the phase loop: one cooperative launch, as many CTAs as fit (at
         // most 1023, the barrier's arrival field)
+        const void *loop = cb8 ? (const void *)k_ot_loop<uint8_t> : (const void *)k_ot_loop<uint16_t>;
         int per_sm = 0;
-        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ot_loop, kOtThreads, 0));
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop, kOtThreads, 0));
         if (per_sm < 1) return fail(PR_ERR_INVALID, "pr_ot: loop kernel does not fit on an SM");
         const int grid = std::min(di.sms * per_sm, 1023);
         const long long limit = spin_limit_cycles();
         void *args[] = {(void *)&p, (void *)&eps, (void *)&limit};
-        PR_CUDA(cudaLaunchCooperativeKernel((const void *)k_ot_loop, dim3(grid), dim3(kOtThreads), args, 0, st));
+        PR_CUDA(cudaLaunchCooperativeKernel(loop, dim3(grid), dim3(kOtThreads), args, 0, st));
     }
     OCtl h;
     PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));

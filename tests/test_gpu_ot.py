@@ -110,3 +110,12 @@ def test_ot_many_phases(prot, nB, nA, eps, seed):
     ref = O.ot(C, nu, mu, eps)
     assert ref["stats"]["phases"] > 3
     assert_ot_parity(r, dense, ref)
+
+
+@pytest.mark.parametrize("nB,nA", [(60, 50), (120, 90)])
+def test_ot_sixteen_bit_storage(prot, nB, nA):
+    """eps = 0.003 (floor(1/eps) = 333 > 252): rounded costs and keys stored in
+    16 bits instead of bytes; thousands of phases."""
+    C, nu, mu = W.ot_euclid_2d(nB, nA, 13)
+    r, dense = gpu_ot(prot, C, nu, mu, 0.003)
+    assert_ot_parity(r, dense, O.ot(C, nu, mu, 0.003))
