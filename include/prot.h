@@ -52,12 +52,16 @@ typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_dtype;
 typedef struct {
     int64_t phases;        /* phases of Sec. 2.2 executed                       */
     int64_t rounds;        /* rounds of step (I) in which a vertex proposed     */
-    int64_t bytes_scanned; /* bytes of rounded-cost rows read by the row scans  */
+    int64_t bytes_scanned; /* bytes of rounded-cost rows the row scans loaded   */
     int64_t rows_scanned;  /* row scans started (one per free vertex per round) */
     int32_t free_at_stop;  /* |B'| when the loop stopped (<= threshold)         */
     int32_t threshold;     /* T = floor(eps * n_rows)                           */
     int32_t loop_ctas;     /* CTAs that ran the phase loop (0: not applicable)  */
     int32_t loop_cluster;  /* 1: they formed one thread-block cluster; 0: grid  */
+    int64_t cells_examined; /* pr_assign: rounded costs the proposal scans
+                               examine, from each scan's start column to the
+                               column it proposes to (inclusive) or to the
+                               row's end; 0 for the other entry points       */
 } pr_stats;
 
 /*

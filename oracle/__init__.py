@@ -33,6 +33,7 @@ MODE_LITERAL = 1
 MODE_CHECK = 2
 MODE_REVERSE = 4
 MODE_SEQUENTIAL = 8
+MODE_EVICT_RESUME = 16
 
 
 class Stats(ctypes.Structure):

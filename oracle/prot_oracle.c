@@ -161,9 +161,10 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
     int32_t *taken = (int32_t *)malloc(sizeof(int32_t) * nA);  /* round */
     int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nA);
     int32_t *mround = (int32_t *)malloc(sizeof(int32_t) * nB);
-    if (!F || !act || !nxt || !mate || !ptr || !prop || !taken || !best || !mround) {
+    int32_t *resume = (int32_t *)calloc((size_t)nB, sizeof(int32_t));
+    if (!F || !act || !nxt || !mate || !ptr || !prop || !taken || !best || !mround || !resume) {
         free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
-        free(taken); free(best); free(mround);
+        free(taken); free(best); free(mround); free(resume);
         return OR_ERR_NOMEM;
     }
     memset(st, 0, sizeof(*st));
@@ -190,6 +191,19 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
         for (int32_t i = 0; i < nf; ++i) {
             int32_t b = F[i];
             mate[b] = -1; ptr[b] = 0; mround[b] = 0;
+            /* OR_MODE_EVICT_RESUME: resume[b] = r > 0 means b was evicted
+             * from column r - 1 in the previous phase.  Every column below r
+             * is then inadmissible for b for good.  Column r - 1 was matched
+             * to b (Eq. 3: y(a) + y(b) = cb) and y(a) dropped when it was
+             * won again.  The scan that gave b column r - 1 passed the
+             * columns below it as inadmissible or taken in an earlier round
+             * (taken columns dropped at that phase's end).  Since then y(b)
+             * has not moved (b was matched), y(a) only drops, and dual
+             * feasibility (Eq. 2) never lets y(a) + y(b) exceed cb + 1, so
+             * none of them returns to equality.  Starting at r gives the
+             * same proposals. */
+            if (mode & OR_MODE_EVICT_RESUME) ptr[b] = resume[b];
+            resume[b] = 0;
         }
         int32_t nact = nf;
         for (int32_t i = 0; i < nf; ++i) act[i] = F[i];
@@ -271,7 +285,7 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
             int32_t a = mate[b];
             if (a < 0) continue;
             int32_t old = match_a[a];
-            if (old >= 0) match_b[old] = -1;
+            if (old >= 0) { match_b[old] = -1; resume[old] = a + 1; }
             match_a[a] = b;
             match_b[b] = a;
         }
@@ -292,7 +306,7 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
     }
 
     free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
-    free(taken); free(best); free(mround);
+    free(taken); free(best); free(mround); free(resume);
     return rc;
 }
 

@@ -17,6 +17,9 @@
 #define OR_MODE_CHECK 2       /* check (I1)/(I2) after every phase          */
 #define OR_MODE_REVERSE 4     /* process B' in descending order             */
 #define OR_MODE_SEQUENTIAL 8  /* the paper's sequential greedy (Lemma 3.4)  */
+#define OR_MODE_EVICT_RESUME 16 /* a row evicted in phase p starts its scan in
+                                   phase p+1 after the column it lost (same
+                                   results; fewer entries examined)         */
 
 typedef struct {
     int64_t phases;       /* phases executed                                  */

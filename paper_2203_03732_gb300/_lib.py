@@ -34,6 +34,7 @@ class PrStats(ctypes.Structure):
         ("threshold", ctypes.c_int32),
         ("loop_ctas", ctypes.c_int32),
         ("loop_cluster", ctypes.c_int32),
+        ("cells_examined", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -78,7 +78,8 @@ struct Ctl {
     long long rounds;
     unsigned long long bytes;
     unsigned long long rows;
-    // PR_PROFILE=1: a %globaltimer split of every round (ns) into kProfSegs
+    unsigned long long cells;  // cost entries the scans examine (start .. answer, or .. row end)
+    // PR_PROFILE=1: a split of every round (SM clock cycles) into kProfSegs
     // segments: round start (bitmaps, keys), item build, row scans,
     // proposals, donations and the rest, grid barrier; then the item count.
     // prof_own sums CTA 0's values over the rounds, prof_max sums the
@@ -89,6 +90,10 @@ struct Ctl {
     unsigned long long prof_rounds;
 };
 constexpr int kProfSegs = 7;
+
+// Profile clock: the SM's cycle counter (segments are durations within one
+// CTA, so counters of different SMs are never compared).
+__device__ __forceinline__ unsigned long long ptimer() { return (unsigned long long)clock64(); }
 
 struct Layout {
     size_t ctl, cb, ka, prop, won, pool, lists, total;
@@ -243,6 +248,7 @@ struct Smem {
     int had_prop, nonfirst, nf_delta, donated;
     unsigned long long bytes;
     unsigned long long rows;
+    unsigned long long cells;
     unsigned long long pub, pub2;
     unsigned long long pacc[4];  // profile: build, scan, proposal, tail ns of this round
     unsigned long long cbar[4][2];  // cluster mode: this CTA's copy of the barrier slots
@@ -465,10 +471,11 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                                          const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
                                          int2 *pool_next, int *pool_cnt, int warps_per_row,
-                                         int rows_per_group, unsigned char *slots, unsigned &mstate) {
+                                         int rows_per_group, unsigned char *slots, unsigned &mstate,
+                                         unsigned long long &cells) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nq = s.njob;
-    const unsigned long long tA = p.profile ? gtimer() : 0;
+    const unsigned long long tA = p.profile ? ptimer() : 0;
     // More jobs than one register group holds go through the shared-memory
     // slots (up to 16 rows in flight instead of rows_per_group); the choice is
     // this CTA's own.  The slot scan reads every unknown y(b) first (the
@@ -547,10 +554,13 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (threadIdx.x < ng) s.job_best[g0 + threadIdx.x] = s.best[threadIdx.x];
     }
     __syncthreads();
-    const unsigned long long tB = p.profile ? gtimer() : 0;
+    const unsigned long long tB = p.profile ? ptimer() : 0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
         const int b = s.job_b[j];
         const int a = s.job_best[j];
+        const int st = s.job_start[j];
+        // entries examined: start .. a, or start .. the row's end
+        cells += a != 0x7FFFFFFF ? (unsigned)(a - st + 1) : (st < p.nA ? (unsigned)(p.nA - st) : 0u);
         if (a != 0x7FFFFFFF) {
             const unsigned long long old = atomicMax(p.prop + a, word_of(R, b));
             const unsigned t = tag_of(old);
@@ -582,7 +592,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         }
     }
     __syncthreads();
-    const unsigned long long tC = p.profile ? gtimer() : 0;
+    const unsigned long long tC = p.profile ? ptimer() : 0;
     if (s.ndon > 0) {
         if (threadIdx.x == 0) s.don_base = atomicAdd(pool_cnt, s.ndon);
         __syncthreads();
@@ -599,7 +609,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (p.profile) {
             s.pacc[1] += tB - tA;
             s.pacc[2] += tC - tB;
-            s.pacc[3] += gtimer() - tC;
+            s.pacc[3] += ptimer() - tC;
         }
     }
     __syncthreads();
@@ -642,6 +652,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     // cluster mode: row slots after the taken set, 128-byte aligned
     unsigned char *slots = dyn + slots_offset(p.ldq, (int)sizeof(CB));
     unsigned mstate = 0;  // cluster mode: this warp's copy state (see run_jobs)
+    unsigned long long cells = 0;  // this thread's count of examined entries (added up at exit)
     Ctl *ctl = p.ctl;
     const unsigned G = gridDim.x;
     const int cta = blockIdx.x;
@@ -674,7 +685,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     if (threadIdx.x == 0) {
         s.nfl[0] = s.nfl[1] = s.nql[0] = s.nql[1] = 0;
         s.njob = s.ndon = 0;
-        s.bytes = s.rows = 0;
+        s.bytes = s.rows = s.cells = 0;
         s.err = 0;
         for (int i = 0; i < 4; ++i) s.cbar[i][0] = s.cbar[i][1] = 0;
         if (SL) {
@@ -707,7 +718,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         bool first_round = true;
         for (;;) {
             ++R;
-            const unsigned long long t_r0 = p.profile ? gtimer() : 0;
+            const unsigned long long t_r0 = p.profile ? ptimer() : 0;
             unsigned *won_now = p.won + (size_t)(R % 3) * p.won_words;
             if (threadIdx.x == 0) {
                 s.pacc[0] = s.pacc[1] = s.pacc[2] = s.pacc[3] = 0;
@@ -759,7 +770,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     wold[i] = 0;
             }
             __syncthreads();
-            const unsigned long long t_r1 = p.profile ? gtimer() : 0;
+            const unsigned long long t_r1 = p.profile ? ptimer() : 0;
             unsigned long long t_mark = t_r1;
             for (int i0 = 0; i0 < nitems; i0 += kBatch) {
                 const int cnt = min(kBatch, nitems - i0);
@@ -798,15 +809,15 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     s.job_tgt[j] = y >= 0 ? y - 1 : -1;
                 }
                 __syncthreads();
-                if (p.profile && threadIdx.x == 0) s.pacc[0] += gtimer() - t_mark;
+                if (p.profile && threadIdx.x == 0) s.pacc[0] += ptimer() - t_mark;
                 run_jobs<CB, SL>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
-                                 &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate);
-                if (p.profile) t_mark = gtimer();
+                                 &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate, cells);
+                if (p.profile) t_mark = ptimer();
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
                                             ((unsigned long long)s.nonfirst << 20) |
                                             ((unsigned long long)s.nf_delta << 40);
-            const unsigned long long t_r2 = p.profile ? gtimer() : 0;
+            const unsigned long long t_r2 = p.profile ? ptimer() : 0;
             unsigned long long seg[kProfSegs] = {};
             if (p.profile && threadIdx.x == 0) {
                 seg[0] = t_r1 - t_r0;
@@ -827,7 +838,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                                    : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated);
             if (!synced) goto done;
             if (p.profile && threadIdx.x == 0) {
-                seg[5] = gtimer() - t_r2;
+                seg[5] = ptimer() - t_r2;
                 // the barrier segment of round R goes to the next round's slot
                 atomicMax(&ctl->prof_slot[(R + 1) & 1][5], seg[5]);
                 if (cta == 0) {
@@ -863,9 +874,12 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         }
     }
 done:
+    if (cells) atomicAdd(&s.cells, cells);
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (s.bytes) atomicAdd(&ctl->bytes, s.bytes);
         if (s.rows) atomicAdd(&ctl->rows, s.rows);
+        if (s.cells) atomicAdd(&ctl->cells, s.cells);
         if (cta == 0) {
             ctl->phases = phase;
             ctl->rounds = rounds;
@@ -1176,6 +1190,7 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
         stats->rounds = h.rounds;
         stats->bytes_scanned = (int64_t)h.bytes;
         stats->rows_scanned = (int64_t)h.rows;
+        stats->cells_examined = (int64_t)h.cells;
         stats->free_at_stop = h.free_at_stop;
         stats->threshold = p.T;
         stats->loop_ctas = cluster ? cfg.cluster : cfg.grid;

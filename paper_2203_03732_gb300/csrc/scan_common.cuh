@@ -121,15 +121,31 @@ __device__ __forceinline__ unsigned eq_mask(uint4 s, uint32_t t2) {
     return m;
 }
 
-// Byte form of the test: bit j of the result is set iff byte j of
-// sat(c + k) equals the target (t4 = target in all four bytes), for the
-// sixteen bytes of one 16-byte load.
+// Byte form of the test on four packed bytes: 0x80 in each byte i with
+// c_i + k_i == t (t4 = t in all four bytes), else 0.  The low seven bits of
+// each byte are added with no carry into the next byte and bit 7 by
+// exclusive or, which gives every byte's sum mod 256; a byte whose true sum
+// reaches 256 (carry out of its bit 7) is masked out, since such a sum never
+// equals a target <= 253.  The zero test of z = sum ^ t4 is exact per byte:
+// (z & 0x7F) + 0x7F sets bit 7 iff the low seven bits are not all zero.
+__device__ __forceinline__ uint32_t byte_marks(uint32_t c, uint32_t k, uint32_t t4) {
+    const uint32_t s7 = (c & 0x7F7F7F7Fu) + (k & 0x7F7F7F7Fu);  // bit 7: carry out of bits 0..6
+    const uint32_t s = s7 ^ ((c ^ k) & 0x80808080u);             // sum mod 256
+    const uint32_t z = s ^ t4;
+    const uint32_t zero = ~(((z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | z | 0x7F7F7F7Fu);
+    const uint32_t ovf = (c & k) | ((c | k) & s7);  // bit 7: carry out of bit 7
+    return zero & ~ovf;
+}
 __device__ __forceinline__ unsigned byte_bits(uint32_t w) {  // bit i = low bit of byte i
     return ((w & 0x01010101u) * 0x01020408u) >> 24;
 }
+// Bit j of the result is set iff byte j of c + k equals the target (t4 =
+// target in all four bytes), for the sixteen bytes of one 16-byte load.
 __device__ __forceinline__ unsigned eq_mask8(uint4 c, uint4 k, uint32_t t4) {
-    return byte_bits(__vcmpeq4(__vaddus4(c.x, k.x), t4)) | (byte_bits(__vcmpeq4(__vaddus4(c.y, k.y), t4)) << 4) |
-           (byte_bits(__vcmpeq4(__vaddus4(c.z, k.z), t4)) << 8) | (byte_bits(__vcmpeq4(__vaddus4(c.w, k.w), t4)) << 12);
+    const uint32_t a = byte_marks(c.x, k.x, t4), b = byte_marks(c.y, k.y, t4);
+    const uint32_t d = byte_marks(c.z, k.z, t4), e = byte_marks(c.w, k.w, t4);
+    if ((a | b | d | e) == 0u) return 0u;
+    return byte_bits(a >> 7) | (byte_bits(b >> 7) << 4) | (byte_bits(d >> 7) << 8) | (byte_bits(e >> 7) << 12);
 }
 
 // Read-only 16-byte load that does not allocate in L1 (streamed rows).

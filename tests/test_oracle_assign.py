@@ -295,6 +295,46 @@ def test_literal_rescan_equals_resume_pointer(seed):
             assert r0["stats"][k] == r1["stats"][k] == r2["stats"][k]
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_evict_resume_equals_resume_pointer(seed):
+    """Starting an evicted row's next scan after the column it lost changes
+    no proposal (every earlier column stays inadmissible, Eq. 2 with growing
+    keys): same matching, duals, phases and rounds, and never more entries
+    examined.  The literal rescan, with every row starting at column 0,
+    examines the most."""
+    n = 90
+    C = W.assignment_euclid_2d(n, seed) if seed % 2 else rand_costs(seed, n, n, "few")
+    for eps in (0.1, 0.02, 0.005):
+        cb = oracle.quantise(C, eps)
+        T = oracle.threshold(eps, n)
+        r0 = oracle.assign_int(cb, T, mode=oracle.MODE_RESUME)
+        r1 = oracle.assign_int(cb, T, mode=oracle.MODE_EVICT_RESUME | oracle.MODE_CHECK)
+        r2 = oracle.assign_int(cb, T, mode=oracle.MODE_EVICT_RESUME | oracle.MODE_REVERSE)
+        for k in ("match_b", "match_a", "y_b", "y_a"):
+            assert np.array_equal(r0[k], r1[k]) and np.array_equal(r0[k], r2[k])
+        for k in ("phases", "rounds", "sum_ni"):
+            assert r0["stats"][k] == r1["stats"][k] == r2["stats"][k]
+        assert r1["stats"]["violations"] == 0
+        assert r1["stats"]["scanned"] == r2["stats"]["scanned"] <= r0["stats"]["scanned"]
+        r3 = oracle.assign_int(cb, T, mode=oracle.MODE_LITERAL)
+        assert r0["stats"]["scanned"] <= r3["stats"]["scanned"]
+
+
+def test_evict_resume_skips_entries_on_a_hand_case():
+    """Two rows, two columns, eps = 0.5 (cb in {0, 1, 2}).  Row 0 takes column
+    0 in phase 1 and loses it to row 1 in phase 2; in phase 3 row 0 starts
+    at column 1 instead of 0, one entry fewer, with the same outcome."""
+    C = np.array([[0.0, 0.0], [0.0, 1.0]])
+    cb = oracle.quantise(C, 0.5)
+    assert cb.tolist() == [[0, 0], [0, 2]]
+    r0 = oracle.assign_int(cb, 0, mode=oracle.MODE_RESUME)
+    r1 = oracle.assign_int(cb, 0, mode=oracle.MODE_EVICT_RESUME)
+    for k in ("match_b", "match_a", "y_b", "y_a"):
+        assert np.array_equal(r0[k], r1[k])
+    assert r0["match_b"].tolist() == [1, 0]
+    assert r0["stats"]["scanned"] - r1["stats"]["scanned"] >= 1
+
+
 def test_sequential_greedy_is_valid_but_different():
     """The paper's own sequential greedy (Lemma 3.4) gives another valid run:
     same invariants and bounds, generally a different matching."""
