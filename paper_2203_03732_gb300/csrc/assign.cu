@@ -62,6 +62,9 @@ template <class CB> constexpr int kChunk = 32 * kPerLoad<CB> * kUnroll;
 // 253, so a saturating byte add cbar + k that reaches 255 can never equal a
 // target, and 255 pads both cbar and keys.
 constexpr int kMaxCbar8 = 252;
+// floor(1/eps) <= 125: cbar <= 125 and keys <= 127 (Lemma 3.2), so cbar + key
+// < 256 and the byte pre-test needs no carry isolation (may_match<true>).
+constexpr int kMaxCbar7 = 125;
 constexpr int kListSm = 1024;             // proposal-list entries kept in shared memory
 constexpr int kKeepMax = 16;              // rows a CTA may keep for its next phase
 constexpr int kBatch = 256;               // items turned into scan jobs at a time
@@ -187,7 +190,7 @@ __device__ __forceinline__ uint4 widen_hi(uint4 x) {
 // in the phase's taken set tk (shared memory; empty in a phase's first
 // round), or -1.  Lane l covers kPerLoad<CB> consecutive columns of each of
 // the kUnroll loads, all issued before any is used.
-template <class CB>
+template <class CB, bool F7>
 // tgt_in < 0: the row's y(b) is not known yet (an evicted row); lane 0 reads
 // it after the row loads are issued, so the two reads overlap.  The target
 // used comes back in tgt_out.
@@ -213,7 +216,7 @@ __device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const
         unsigned m = 0;
         if (idx < ldq) {
             const uint4 kv = *reinterpret_cast<const uint4 *>(ks + idx);
-            m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8(cv[u], kv, t2);
+            m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8<F7>(cv[u], kv, t2);
         }
         const int lo = start - idx;
         if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
@@ -421,7 +424,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned par
 // Lowest candidate column >= start in the slot holding cbar[s_al .. ldq) of
 // one row (the test of warp_scan_chunk), or -1.  Four 16-byte shared loads
 // per lane are in flight per step.
-template <class CB>
+template <class CB, bool F7>
 __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const CB *ks, const unsigned *tk,
                                               bool check_taken, int s_al, int start, int ldq, uint32_t tgt,
                                               int lane) {
@@ -443,7 +446,7 @@ __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const C
             unsigned m = 0;
             if (idx < ldq) {
                 const uint4 kv = *reinterpret_cast<const uint4 *>(ks + idx);
-                m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8(cv[u], kv, t2);
+                m = W == 8 ? eq_mask(add_keys(cv[u], kv), t2) : eq_mask8<F7>(cv[u], kv, t2);
             }
             const int lo = start - idx;
             if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
@@ -466,7 +469,7 @@ constexpr long long kCopyWaitCycles = 2000000000ll;
 // with warps_per_row warps per row; cluster form: one row per warp through
 // its slot); then every proposal (atomicMax) or relabel at once; then the
 // pool donations.
-template <class CB, bool SL>
+template <class CB, bool SL, bool F7>
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
@@ -507,7 +510,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                     if (mbar_wait(&s.mbar[warp], mstate & 1u, kCopyWaitCycles)) {
                         mstate ^= 1u;
                         my_bytes += bytes;
-                        a = warp_scan_slot<CB>(slot, ks, tk, R > Rps, s_al, start, p.ldq, tgt, lane);
+                        a = warp_scan_slot<CB, F7>(slot, ks, tk, R > Rps, s_al, start, p.ldq, tgt, lane);
                     } else {
                         mstate |= 2u;
                         if (lane == 0) record_error(&p.ctl->head, PR_ERR_TIMEOUT);
@@ -537,7 +540,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
                 my_bytes += sizeof(CB) * (unsigned long long)min(kChunk<CB>, p.ldq - c0);
                 int t_used;
-                const int a = warp_scan_chunk<CB>(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, p.y_b + b,
+                const int a = warp_scan_chunk<CB, F7>(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, p.y_b + b,
                                                   t_used, lane);
                 tgt = t_used;
                 if (a >= 0) {
@@ -641,7 +644,7 @@ __host__ __device__ inline size_t slots_offset(int ldq, int key_bytes) {
 // shared memory) instead of a cooperative grid.  SL: a CTA whose jobs exceed
 // one register group scans them from per-warp shared-memory slots filled by
 // bulk copies (always with CL).
-template <class CB, bool CL, bool SL>
+template <class CB, bool CL, bool SL, bool F7>
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -810,7 +813,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 }
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += ptimer() - t_mark;
-                run_jobs<CB, SL>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
+                run_jobs<CB, SL, F7>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
                                  &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate, cells);
                 if (p.profile) t_mark = ptimer();
             }
@@ -993,14 +996,30 @@ struct PhaseCfg {
     size_t smem = 0;
 };
 
-template <class CB, bool CL, bool SL>
+template <class CB, bool CL, bool SL, bool F7>
 pr_status set_phase_attrs(size_t smem) {
-    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return PR_OK;
 }
 
-// Largest cluster (16, else 8) of k_phases<CB, true, true> the device can hold, or 0.
+// The phase kernel for the storage type (cb8: bytes), the form (cl: one
+// cluster, sl: row slots) and the byte pre-test (f7: floor(1/eps) <= 125).
+const void *phase_kernel(bool cb8, bool cl, bool sl, bool f7) {
+    if (!cb8)
+        return cl ? (const void *)k_phases<uint16_t, true, true, false>
+                  : sl ? (const void *)k_phases<uint16_t, false, true, false>
+                       : (const void *)k_phases<uint16_t, false, false, false>;
+    if (f7)
+        return cl ? (const void *)k_phases<uint8_t, true, true, true>
+                  : sl ? (const void *)k_phases<uint8_t, false, true, true>
+                       : (const void *)k_phases<uint8_t, false, false, true>;
+    return cl ? (const void *)k_phases<uint8_t, true, true, false>
+              : sl ? (const void *)k_phases<uint8_t, false, true, false>
+                   : (const void *)k_phases<uint8_t, false, false, false>;
+}
+
+// Largest cluster (16, else 8) of k_phases<CB, true, true, false> the device can hold, or 0.
 template <class CB>
 int max_phase_cluster(size_t smem) {
     for (int cs : {16, 8}) {
@@ -1016,7 +1035,7 @@ int max_phase_cluster(size_t smem) {
         c.attrs = at;
         c.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true, true>, &c) == cudaSuccess && n >= 1)
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true, true, false>, &c) == cudaSuccess && n >= 1)
             return cs;
         cudaGetLastError();  // clear a refusal of this size
     }
@@ -1036,16 +1055,19 @@ pr_status phase_cfg(PhaseCfg &cfg) {
     }
     const DeviceInfo &di = device_info();
     const size_t smem = (size_t)di.max_smem_optin;  // Smem + the key copy; see smem_bytes()
-    pr_status rc = set_phase_attrs<uint8_t, false, false>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, false>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, true>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true>(smem);
-    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true, true>(smem);
+    pr_status rc = set_phase_attrs<uint8_t, false, false, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, false, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, true, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true, true, false>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true, true>(smem);
     if (rc != PR_OK) return rc;
     int per_sm = 0, per_sm16 = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false, false>, kThreads, smem));
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false, false, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false, false, false>, kThreads, smem));
     if (per_sm16 < per_sm) per_sm = per_sm16;
     if (per_sm < 1) return fail(PR_ERR_INVALID, "phase kernel does not fit on an SM");
     int grid = di.sms * per_sm;
@@ -1108,6 +1130,7 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
         p.profile = (pf && *pf == '1') ? 1 : 0;
     }
     const bool cb8 = K <= kMaxCbar8;  // every cbar fits one byte
+    const bool f7 = cb8 && K <= kMaxCbar7;  // and cbar + key < 256 on every real column
 
     const DeviceInfo &di = device_info();
     k_init<<<di.sms * 2, 256, 0, st>>>(p, row_to_col);
@@ -1156,14 +1179,14 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
         c.stream = st;
         c.attrs = at;
         c.numAttrs = 1;
-        if (cb8) PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint8_t, true, true>, p, warps_per_row, rows_per_group));
-        else PR_CUDA(cudaLaunchKernelEx(&c, k_phases<uint16_t, true, true>, p, warps_per_row, rows_per_group));
+        Params pc = p;
+        void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
+        PR_CUDA(cudaLaunchKernelExC(&c, phase_kernel(cb8, true, true, f7), args));
     } else {
         Params pc = p;
         void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
         const bool sl = use_slots_in_grid(p.nslots);
-        const void *fn = sl ? (cb8 ? (const void *)k_phases<uint8_t, false, true> : (const void *)k_phases<uint16_t, false, true>)
-                            : (cb8 ? (const void *)k_phases<uint8_t, false, false> : (const void *)k_phases<uint16_t, false, false>);
+        const void *fn = phase_kernel(cb8, false, sl, f7);
         const size_t smem = sl ? slots_offset(p.ldq, kb) + (size_t)p.nslots * p.slot_bytes : smem_bytes(p.ldq, kb);
         PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, smem, st));
     }

@@ -141,11 +141,30 @@ __device__ __forceinline__ unsigned byte_bits(uint32_t w) {  // bit i = low bit 
 }
 // Bit j of the result is set iff byte j of c + k equals the target (t4 =
 // target in all four bytes), for the sixteen bytes of one 16-byte load.
-__device__ __forceinline__ unsigned eq_mask8(uint4 c, uint4 k, uint32_t t4) {
+__device__ __forceinline__ unsigned eq_mask8_exact(uint4 c, uint4 k, uint32_t t4) {
     const uint32_t a = byte_marks(c.x, k.x, t4), b = byte_marks(c.y, k.y, t4);
     const uint32_t d = byte_marks(c.z, k.z, t4), e = byte_marks(c.w, k.w, t4);
-    if ((a | b | d | e) == 0u) return 0u;
     return byte_bits(a >> 7) | (byte_bits(b >> 7) << 4) | (byte_bits(d >> 7) << 8) | (byte_bits(e >> 7) << 12);
+}
+// A first test that most loads settle: nonzero iff some byte of the four
+// words may match.  (z - 0x01..) & ~z & 0x80.. is nonzero iff some byte of
+// z is zero (exact as an existence test).  F7 (floor(1/eps) <= 125: cbar <=
+// 125, keys <= 127): a plain add has no carry between the bytes of real
+// columns (padding bytes 0xFF + 0xFF sit above them and never equal a
+// target), so z = (c + k) ^ t4.  Otherwise z is formed from the per-byte sum
+// mod 256, and a sum that reached 256 can pass; the exact marks settle it.
+__device__ __forceinline__ uint32_t zero_byte(uint32_t z) { return (z - 0x01010101u) & ~z & 0x80808080u; }
+template <bool F7>
+__device__ __forceinline__ uint32_t may_match(uint32_t c, uint32_t k, uint32_t t4) {
+    if (F7) return zero_byte((c + k) ^ t4);
+    return zero_byte((((c & 0x7F7F7F7Fu) + (k & 0x7F7F7F7Fu)) ^ ((c ^ k) & 0x80808080u)) ^ t4);
+}
+template <bool F7 = false>
+__device__ __forceinline__ unsigned eq_mask8(uint4 c, uint4 k, uint32_t t4) {
+    if ((may_match<F7>(c.x, k.x, t4) | may_match<F7>(c.y, k.y, t4) | may_match<F7>(c.z, k.z, t4) |
+         may_match<F7>(c.w, k.w, t4)) == 0u)
+        return 0u;
+    return eq_mask8_exact(c, k, t4);
 }
 
 // Read-only 16-byte load that does not allocate in L1 (streamed rows).

@@ -303,3 +303,15 @@ def test_rounding_on_and_next_to_multiples_of_eps(prot, eps, dtype):
     C = np.clip(C, 0, 1).astype(dtype)
     C[0, :4] = [0.0, -0.0, 1.0, np.finfo(dtype).tiny / 4]
     assert_parity(gpu_solve(prot, C, eps), oracle.assign(C, eps))
+
+
+@pytest.mark.parametrize("K", [125, 126, 252, 253])
+def test_byte_test_forms_at_their_limits(prot, K):
+    """floor(1/eps) = 125 is the largest for the plain-add byte pre-test,
+    126 .. 252 take the carry-isolated one, 253 switches to 16-bit storage:
+    parity and the exact examined-entry count on either side of each limit."""
+    eps = 1.0 / (K + 0.5)
+    C = W.assignment_euclid_2d(1500, 60 + K)
+    got = gpu_solve(prot, C, eps)
+    assert_parity(got, oracle.assign(C, eps))
+    assert_cells(got, C, eps)
