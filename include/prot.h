@@ -103,6 +103,24 @@ pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int
                     int32_t *y_col, double *cost, pr_stats *stats, void *ws, size_t ws_bytes,
                     void *stream);
 
+/*
+ * pr_dual_bound -- the a-posteriori certificate of a pr_assign solve
+ * (Lemma 3.1).  The duals it returns satisfy Eq. (2), y(a) + y(b) <= cbar +
+ * eps on every edge; summed over any matching that covers the rows (column
+ * duals are <= 0) this gives
+ *     L = eps * (sum y_row + sum y_col - n_rows) <= OPT(cbar) <= OPT(c),
+ * a lower bound on the optimal cost that needs no optimal solver, so that
+ * cost - L bounds the solve's additive error from above.
+ *   y_row [n_rows], y_col [n_cols]  the solve's integer duals (units of eps)
+ *   eps        the solve's eps
+ *   cost       [1] the solve's cost, or NULL
+ *   out        [2] out: out[0] = L, out[1] = cost - L (a NaN when cost is NULL)
+ * The sums are exact 64-bit integer sums; L is one FP64 product, the gap one
+ * FP64 difference.  All pointers are device pointers.  Asynchronous.
+ */
+pr_status pr_dual_bound(const int32_t *y_row, const int32_t *y_col, int32_t n_rows, int32_t n_cols,
+                        double eps, const double *cost, double *out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched form: many independent square problems in one persistent launch.  */
 /* ------------------------------------------------------------------------ */

@@ -6,6 +6,8 @@ Optimal Transport" (arXiv 2203.03732).  The solver runs in the CUDA library
 torch-facing wrapper (device memory, streams, argument marshalling).
 
     assign(C, eps)                     one problem
+    assign_within(C, delta)            one problem, cost <= OPT + delta * n_rows
+    dual_bound(result, eps)            lower bound on OPT from a result's duals
     assign_batched(C, sizes, eps)      many square problems, one launch
     assign_batched_points(XA, XB, sizes, eps)   the same with costs from points
     assignment_loss(X, Y, eps)         differentiable mean matched squared distance
@@ -16,7 +18,8 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["assign", "assign_batched", "assign_batched_points", "assign_backward", "ot",
+__all__ = ["assign", "assign_within", "dual_bound", "assign_batched", "assign_batched_points",
+           "assign_backward", "ot",
            "assignment_loss", "AssignLoss", "Workspace", "PrError"]
 
 PrError = _lib.PrError
@@ -111,6 +114,38 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
     if host_in:
         res = {k: (v.cpu() if hasattr(v, "cpu") else v) for k, v in res.items()}
     return res
+
+
+def dual_bound(result, eps: float):
+    """Lemma 3.1's certificate of an `assign` result: a lower bound L on the
+    optimal cost from the returned duals, and the bound cost - L on the
+    solve's additive error (both FP64 scalar tensors on the result's device;
+    for a host result they are copied back).  No optimal solver is needed."""
+    torch = _torch()
+    L = _lib.load()
+    host = not result["y_row"].is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else result["y_row"].device
+    yb = result["y_row"].to(dev, dtype=torch.int32).contiguous()
+    ya = result["y_col"].to(dev, dtype=torch.int32).contiguous()
+    cost = result["cost"].to(dev, dtype=torch.float64).reshape(())
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    rc = L.pr_dual_bound(yb.data_ptr(), ya.data_ptr(), yb.numel(), ya.numel(), float(eps),
+                         cost.data_ptr(), out.data_ptr(), _stream_handle(torch, dev))
+    _lib.check(rc, "pr_dual_bound")
+    if host:
+        out = out.cpu()
+    return {"lower_bound": out[0], "gap_bound": out[1]}
+
+
+def assign_within(C, delta: float, **kw):
+    """A matching whose cost is within delta * n_rows of the optimum (costs
+    in [0, 1]).  The main routine with parameter eps is a 3 eps
+    approximation (Sec. 2.1, Lemma 3.1); the paper's introduction obtains an
+    eps approximation by running it with eps / 3, as this does with delta.
+    Keyword arguments go to `assign`."""
+    if not (0.0 < delta < 3.0):
+        raise ValueError("need 0 < delta < 3")
+    return assign(C, delta / 3.0, **kw)
 
 
 def _tune_cache_path():
