@@ -288,6 +288,29 @@ def run_extras(a, torch, prot, W, dev, stream):
                            "bytes_scanned": r["stats"]["bytes_scanned"]}
     ex["assign_eps_sweep"] = sweep
     del C
+    # the same workload with the costs formed on the device from the points
+    A, B = W.points_uniform(a.n, a.n, 2, a.seed, dtype=np.float32)
+    XA, XB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    r = prot.assign_points(XA, XB, a.eps, ws=ws)
+    outp = {k: v for k, v in r.items() if k != "stats"}
+    ms = timed(torch, stream, lambda: prot.assign_points(XA, XB, a.eps, ws=ws, sync=False, out=outp), 10)
+    XA_h, XB_h = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    r2c_h = torch.empty(a.n, dtype=torch.int32).pin_memory()
+    cost_h = torch.empty((), dtype=torch.float64).pin_memory()
+    XA2, XB2 = torch.empty_like(XA), torch.empty_like(XB)
+
+    def e2e_points():
+        XA2.copy_(XA_h, non_blocking=True)
+        XB2.copy_(XB_h, non_blocking=True)
+        prot.assign_points(XA2, XB2, a.eps, ws=ws, sync=False, out=outp)
+        r2c_h.copy_(outp["row_to_col"], non_blocking=True)
+        cost_h.copy_(outp["cost"], non_blocking=True)
+    ms_e2e = timed(torch, stream, e2e_points, 10)
+    ex["assign_points"] = {"workload": f"the same {a.n} + {a.n} points (FP32), Euclidean / max, eps={a.eps}, "
+                                       "costs formed on the device (no n^2 input)",
+                           "ms": ms, "e2e_ms": ms_e2e, "h2d_bytes": int(A.nbytes + B.nbytes),
+                           "phases": r["stats"]["phases"], "cells_examined": r["stats"]["cells_examined"]}
+    del XA, XB, XA2, XB2
 
     # batched: 512 problems, n_i uniform in [64, 2048], 3-D points, sq. Euclidean, eps 0.01
     sizes = W.batched_sizes(512, 64, 2048, seed=0)

@@ -184,6 +184,28 @@ pr_status pr_assign_batched_points(const float *XA, const float *XB, int32_t dim
                                    size_t ws_bytes, void *stream);
 
 /*
+ * pr_assign_points -- pr_assign with the costs formed from two point sets on
+ * the device instead of read from a stored matrix (Sec. 1: c(a,b) is the
+ * distance of a and b; Sec. 5 draws points in the unit square).  XB holds
+ * the n_rows row points (the proposing side B) and XA the n_cols column
+ * points (A), dim FP32 coordinates each, row-major.  d = sum_k (xb_k -
+ * xa_k)^2 in FP32, one IEEE operation at a time in ascending k (PR_EUCLIDEAN:
+ * its IEEE square root); the rounded costs of Eq. (1) use c = RN32(d / max d)
+ * so that the largest cost is 1.  No n_rows x n_cols input exists: the
+ * rounded matrix is written straight into the workspace.
+ *   cost       [1] out: the FP64 sum over the rows of the matched d,
+ *              re-evaluated in FP64 (input units)
+ *   ws, ws_bytes  >= pr_assign_workspace(n_rows, n_cols)
+ * Other arguments, outputs and errors as pr_assign.  Coordinates that make
+ * a distance non-finite give PR_ERR_INVALID (reported when the call
+ * synchronises).
+ */
+pr_status pr_assign_points(const float *XA, const float *XB, int32_t dim, pr_metric metric, int32_t n_rows,
+                           int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
+                           int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/*
  * pr_assign_batched_autotune -- picks the batched solver's launch shape for a
  * given batch: runs the solve once per candidate (threads per CTA in {128,
  * 256, 512, 1024} x resident CTAs per SM in {1, 2, 3, 4}; shapes that do not

@@ -7,6 +7,7 @@ torch-facing wrapper (device memory, streams, argument marshalling).
 
     assign(C, eps)                     one problem
     assign_within(C, delta)            one problem, cost <= OPT + delta * n_rows
+    assign_points(XA, XB, eps)         one problem with the costs formed from points
     dual_bound(result, eps)            lower bound on OPT from a result's duals
     assign_batched(C, sizes, eps)      many square problems, one launch
     assign_batched_points(XA, XB, sizes, eps)   the same with costs from points
@@ -18,7 +19,7 @@ import ctypes
 
 from . import _lib
 
-__all__ = ["assign", "assign_within", "dual_bound", "assign_batched", "assign_batched_points",
+__all__ = ["assign", "assign_within", "assign_points", "dual_bound", "assign_batched", "assign_batched_points",
            "assign_backward", "ot",
            "assignment_loss", "AssignLoss", "Workspace", "PrError"]
 
@@ -108,6 +109,51 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
                      ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
                      _stream_handle(torch, dev))
     _lib.check(rc, "pr_assign")
+    res = dict(out)
+    if sync:
+        res["stats"] = st.as_dict()
+    if host_in:
+        res = {k: (v.cpu() if hasattr(v, "cpu") else v) for k, v in res.items()}
+    return res
+
+
+def assign_points(XA, XB, eps: float, *, metric: str = "euclidean", sync: bool = True,
+                  ws: Workspace | None = None, out=None):
+    """`assign` with the costs formed on the device from point sets: XB
+    (n_rows, dim) are the rows, XA (n_cols, dim) the columns, FP32.  The
+    cost is the distance ("euclidean" or "sqeuclidean") scaled by its largest
+    value, rounded by Eq. (1); the returned cost is the matched distance sum
+    in input units (FP64).  CPU tensors are copied to the current CUDA device
+    and the results back."""
+    torch = _torch()
+    L = _lib.load()
+    host_in = not XB.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host_in else XB.device
+    XBd = XB.to(dev, dtype=torch.float32, non_blocking=True).contiguous()
+    XAd = XA.to(dev, dtype=torch.float32, non_blocking=True).contiguous()
+    if XBd.dim() != 2 or XAd.dim() != 2 or XBd.shape[1] != XAd.shape[1]:
+        raise ValueError("XA, XB must be (n, dim) with the same dim")
+    m = {"sqeuclidean": _lib.PR_SQEUCLIDEAN, "euclidean": _lib.PR_EUCLIDEAN}[metric]
+    nB, nA, d = XBd.shape[0], XAd.shape[0], XBd.shape[1]
+    need = L.pr_assign_workspace(nB, nA)
+    if need == 0:
+        raise ValueError("invalid sizes: need 1 <= n_rows <= n_cols <= 2^24")
+    wsb = (ws or _workspace(dev)).get(need)
+    if out is None:
+        out = dict(
+            row_to_col=torch.empty(nB, dtype=torch.int32, device=dev),
+            col_to_row=torch.empty(nA, dtype=torch.int32, device=dev),
+            y_row=torch.empty(nB, dtype=torch.int32, device=dev),
+            y_col=torch.empty(nA, dtype=torch.int32, device=dev),
+            cost=torch.empty((), dtype=torch.float64, device=dev),
+        )
+    st = _lib.PrStats()
+    rc = L.pr_assign_points(XAd.data_ptr(), XBd.data_ptr(), d, m, nB, nA, float(eps),
+                            out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
+                            out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["cost"].data_ptr(),
+                            ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
+                            _stream_handle(torch, dev))
+    _lib.check(rc, "pr_assign_points")
     res = dict(out)
     if sync:
         res["stats"] = st.as_dict()

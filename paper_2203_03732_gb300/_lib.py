@@ -87,6 +87,8 @@ SIGNATURES = {
                                                   ctypes.POINTER(PrBatchedTune), ctypes.POINTER(ctypes.c_float),
                                                   _vp, _sz, _vp]),
     "pr_dual_bound": (ctypes.c_int, [_vp, _vp, _i32, _i32, _dbl, _vp, _vp, _vp]),
+    "pr_assign_points": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
+                                        _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),
     "pr_set_kernel_events": (None, [_vp, _vp]),
     "pr_last_error": (ctypes.c_char_p, []),

@@ -46,6 +46,7 @@
 #include "prot_internal.cuh"
 #include "scan_common.cuh"
 #include "quantise.cuh"
+#include "points.cuh"
 
 namespace prot {
 namespace {
@@ -82,6 +83,8 @@ struct Ctl {
     unsigned long long bytes;
     unsigned long long rows;
     unsigned long long cells;  // cost entries the scans examine (start .. answer, or .. row end)
+    unsigned maxbits;          // points source: bits of the largest distance (FP32, >= 0)
+    int pad1;
     // PR_PROFILE=1: a split of every round (SM clock cycles) into kProfSegs
     // segments: round start (bitmaps, keys), item build, row scans,
     // proposals, donations and the rest, grid barrier; then the item count.
@@ -944,10 +947,25 @@ __device__ __forceinline__ int block_exclusive_scan(int flag, int *warp_tot, int
     return r;
 }
 
+// The matched costs k_finish adds up: from the input matrix, or the FP64
+// distance of the matched points (input units).
 template <class T>
+struct MatrixCost {
+    const T *C;
+    long long ldc;
+    __device__ double operator()(int b, int a) const { return (double)C[(long long)b * ldc + a]; }
+};
+struct PointsCost {
+    const float *XA, *XB;
+    int dim, squared;
+    __device__ double operator()(int b, int a) const {
+        return dist_f64(XB + (long long)b * dim, XA + (long long)a * dim, dim, squared);
+    }
+};
+
+template <class Src>
 __global__ void __launch_bounds__(kFinThreads)
-k_finish(Params p, const T *__restrict__ C, long long ldc, int *match_b, int *match_a,
-         int *free_b, int *free_a, double *cost) {
+k_finish(Params p, Src src, int *match_b, int *match_a, int *free_b, int *free_a, double *cost) {
     __shared__ int warp_tot[32];
     __shared__ int total;
     __shared__ double part[kFinThreads];
@@ -977,7 +995,7 @@ k_finish(Params p, const T *__restrict__ C, long long ldc, int *match_b, int *ma
     __syncthreads();
     double acc = 0.0;
     for (int b = threadIdx.x; b < p.nB; b += kFinThreads)
-        acc = __dadd_rn(acc, (double)C[(long long)b * ldc + match_b[b]]);
+        acc = __dadd_rn(acc, src(b, match_b[b]));
     part[threadIdx.x] = acc;
     __syncthreads();
     for (int w = kFinThreads / 2; w > 0; w >>= 1) {
@@ -985,6 +1003,74 @@ k_finish(Params p, const T *__restrict__ C, long long ldc, int *match_b, int *ma
         __syncthreads();
     }
     if (threadIdx.x == 0) *cost = part[0];
+}
+
+// ---------------------------------------------------------------------------
+// Costs from points (points.cuh), over the same (row, group of 8 columns)
+// grid stride as k_quantise: first the largest distance, then Eq. (1) on
+// c = RN32(d / max d), exactly as for a stored FP32 cost.
+// ---------------------------------------------------------------------------
+__global__ void k_points_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim, int squared,
+                             int nB, int nA, int ldq, unsigned *maxbits) {
+    const long long groups = (long long)nB * (ldq >> 3);
+    float m = 0.0f;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / (ldq >> 3));
+        const int a0 = (int)(g - (long long)b * (ldq >> 3)) << 3;
+        const float *xb = XB + (long long)b * dim;
+        for (int j = 0; j < 8 && a0 + j < nA; ++j)
+            m = fmaxf(m, dist_f32(xb, XA + (long long)(a0 + j) * dim, dim, squared));
+    }
+    // non-negative floats order like their bit patterns (NaN is dropped by fmaxf)
+    const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxbits, mx);
+}
+
+template <class CB>
+__global__ void k_points_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim, int squared,
+                               int nB, int nA, int ldq, const unsigned *__restrict__ maxbits, EpsSplit e,
+                               CB *__restrict__ cb, WsHead *head) {
+    constexpr uint32_t kPad = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
+    const long long groups = (long long)nB * (ldq >> 3);
+    const float M = __uint_as_float(*maxbits);
+    bool bad = false;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / (ldq >> 3));
+        const int a0 = (int)(g - (long long)b * (ldq >> 3)) << 3;
+        const float *xb = XB + (long long)b * dim;
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int a = a0 + j;
+            if (a < nA) {
+                const float d = dist_f32(xb, XA + (long long)a * dim, dim, squared);
+                if (!(d >= 0.0f && d <= M)) {  // NaN or infinite coordinates
+                    bad = true;
+                    h[j] = 0;
+                    continue;
+                }
+                const float c = M > 0.0f ? __fdiv_rn(d, M) : 0.0f;
+                h[j] = quantise_fbits(__float_as_uint(c), e);
+                if (h[j] == 0xFFFFFFFFu) {  // c not in [0, 1]: an infinite largest distance
+                    bad = true;
+                    h[j] = 0;
+                }
+            } else {
+                h[j] = kPad;
+            }
+        }
+        if (sizeof(CB) == 1) {
+            *reinterpret_cast<uint2 *>(cb + (long long)b * ldq + a0) =
+                make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
+                           h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
+        } else {
+            *reinterpret_cast<uint4 *>(cb + (long long)b * ldq + a0) =
+                make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
+    }
+    if (bad) record_error(head, PR_ERR_INVALID);
 }
 
 // ---------------------------------------------------------------------------
@@ -1113,12 +1199,26 @@ bool use_slots_in_grid(int nslots) {
     return !(m && strcmp(m, "regs") == 0);
 }
 
-// Everything after the argument checks, shared by pr_assign and
-// pr_assign_noalloc: p holds the workspace regions and sizes; this fills the
-// scalars, then enqueues init, rounding, the phase loop, decode and finish.
-pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, double eps, const PhaseCfg &cfg,
+// Where the costs come from: a matrix (C, dt, ldc) or two point sets (XA the
+// columns, XB the rows, `dim` FP32 coordinates each).
+struct CostSource {
+    const void *C = nullptr;
+    pr_dtype dt = PR_F64;
+    int64_t ldc = 0;
+    const float *XA = nullptr, *XB = nullptr;
+    int dim = 0, squared = 0;
+    bool points = false;
+};
+
+// Everything after the argument checks, shared by pr_assign, pr_assign_points
+// and pr_assign_noalloc: p holds the workspace regions and sizes; this fills
+// the scalars, then enqueues init, rounding, the phase loop, decode and finish.
+pr_status launch_solve(Params &p, const CostSource &src, double eps, const PhaseCfg &cfg,
                        int32_t *row_to_col, int32_t *col_to_row, int32_t *y_col, double *cost,
                        pr_stats *stats, bool profile_ok, const char *who, cudaStream_t st) {
+    const void *C = src.C;
+    const pr_dtype dt = src.dt;
+    const int64_t ldc = src.ldc;
     const int n_rows = p.nB, n_cols = p.nA;
     p.T = (int)floor(eps * (double)n_rows);
     const long long K = (long long)floor(1.0 / eps);
@@ -1139,7 +1239,18 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
     const long long want = groups / 256 + 1;
     const int qgrid = (int)(want < (long long)di.sms * 16 ? want : (long long)di.sms * 16);
     void *cbw = const_cast<void *>(p.cb);
-    if (dt == PR_F64 && cb8)
+    if (src.points) {
+        const EpsSplit e = make_eps_split(eps);
+        k_points_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols, p.ldq,
+                                            &p.ctl->maxbits);
+        PR_CUDA(cudaGetLastError());
+        if (cb8)
+            k_points_quant<uint8_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
+                                                           p.ldq, &p.ctl->maxbits, e, (uint8_t *)cbw, &p.ctl->head);
+        else
+            k_points_quant<uint16_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
+                                                            p.ldq, &p.ctl->maxbits, e, (uint16_t *)cbw, &p.ctl->head);
+    } else if (dt == PR_F64 && cb8)
         launch_quantise<double, uint8_t>((const double *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint8_t *)cbw,
                                          &p.ctl->head, qgrid, st);
     else if (dt == PR_F64)
@@ -1197,12 +1308,15 @@ pr_status launch_solve(Params &p, const void *C, pr_dtype dt, int64_t ldc, doubl
     // completion scratch: the first CTA's list region (free after the loop)
     int *free_b = p.lists;
     int *free_a = p.lists + n_rows;
-    if (dt == PR_F64)
-        k_finish<double><<<1, kFinThreads, 0, st>>>(p, (const double *)C, ldc, row_to_col, col_to_row,
-                                                    free_b, free_a, cost);
+    if (src.points)
+        k_finish<PointsCost><<<1, kFinThreads, 0, st>>>(p, PointsCost{src.XA, src.XB, src.dim, src.squared},
+                                                         row_to_col, col_to_row, free_b, free_a, cost);
+    else if (dt == PR_F64)
+        k_finish<MatrixCost<double>><<<1, kFinThreads, 0, st>>>(p, MatrixCost<double>{(const double *)C, ldc},
+                                                                row_to_col, col_to_row, free_b, free_a, cost);
     else
-        k_finish<float><<<1, kFinThreads, 0, st>>>(p, (const float *)C, ldc, row_to_col, col_to_row,
-                                                   free_b, free_a, cost);
+        k_finish<MatrixCost<float>><<<1, kFinThreads, 0, st>>>(p, MatrixCost<float>{(const float *)C, ldc},
+                                                               row_to_col, col_to_row, free_b, free_a, cost);
     PR_CUDA(cudaGetLastError());
 
     if (stats) {
@@ -1237,27 +1351,30 @@ extern "C" size_t pr_assign_workspace(int32_t n_rows, int32_t n_cols) {
     return make_layout(n_rows, n_cols, cfg.grid).total;
 }
 
-extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
-                               int32_t n_cols, double eps, int32_t *row_to_col,
-                               int32_t *col_to_row, int32_t *y_row, int32_t *y_col, double *cost,
-                               pr_stats *stats, void *ws, size_t ws_bytes, void *stream) {
-    if (!C || !row_to_col || !col_to_row || !y_row || !y_col || !cost)
-        return fail(PR_ERR_INVALID, "pr_assign: NULL pointer argument");
-    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign: bad dtype");
+namespace prot {
+namespace {
+
+// pr_assign and pr_assign_points after their own source checks: sizes, eps,
+// workspace, then the solve.
+pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, double eps,
+                        int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
+                        double *cost, pr_stats *stats, void *ws, size_t ws_bytes, void *stream,
+                        const char *who) {
+    if (!row_to_col || !col_to_row || !y_row || !y_col || !cost)
+        return fail(PR_ERR_INVALID, "%s: NULL pointer argument", who);
     if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24) - 1)
-        return fail(PR_ERR_INVALID, "pr_assign: need 1 <= n_rows <= n_cols < 2^24");
-    if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign: ldc < n_cols");
+        return fail(PR_ERR_INVALID, "%s: need 1 <= n_rows <= n_cols < 2^24", who);
     if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
-        return fail(PR_ERR_INVALID, "pr_assign: need 0 < eps < 1 and floor(1/eps) <= 32766");
+        return fail(PR_ERR_INVALID, "%s: need 0 < eps < 1 and floor(1/eps) <= 32766", who);
     PhaseCfg cfg;
     pr_status rc = phase_cfg(cfg);
     if (rc != PR_OK) return rc;
     const Layout L = make_layout(n_rows, n_cols, cfg.grid);
     if (smem_bytes(L.ldq) > cfg.smem)
-        return fail(PR_ERR_INVALID, "pr_assign: n_cols = %d exceeds the shared-memory key copy (max %d)",
+        return fail(PR_ERR_INVALID, "%s: n_cols = %d exceeds the shared-memory key copy (max %d)", who,
                     n_cols, (int)((cfg.smem - smem_bytes(0)) * 16 / 33) & ~31);
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
-        return fail(PR_ERR_WORKSPACE, "pr_assign: workspace NULL, not 256-byte aligned or < %zu bytes",
+        return fail(PR_ERR_WORKSPACE, "%s: workspace NULL, not 256-byte aligned or < %zu bytes", who,
                     L.total);
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
@@ -1276,8 +1393,43 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
-    return launch_solve(p, C, dt, ldc, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, true,
-                        "pr_assign", st);
+    return launch_solve(p, src, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, true, who, st);
+}
+
+}  // namespace
+}  // namespace prot
+
+extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                               int32_t n_cols, double eps, int32_t *row_to_col,
+                               int32_t *col_to_row, int32_t *y_row, int32_t *y_col, double *cost,
+                               pr_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+    if (!C) return fail(PR_ERR_INVALID, "pr_assign: NULL pointer argument");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign: bad dtype");
+    if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign: ldc < n_cols");
+    CostSource src;
+    src.C = C;
+    src.dt = dt;
+    src.ldc = ldc;
+    return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
+                         ws_bytes, stream, "pr_assign");
+}
+
+extern "C" pr_status pr_assign_points(const float *XA, const float *XB, int32_t dim, pr_metric metric,
+                                      int32_t n_rows, int32_t n_cols, double eps, int32_t *row_to_col,
+                                      int32_t *col_to_row, int32_t *y_row, int32_t *y_col, double *cost,
+                                      pr_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+    if (!XA || !XB) return fail(PR_ERR_INVALID, "pr_assign_points: NULL point pointer");
+    if (dim < 1 || dim > 4096) return fail(PR_ERR_INVALID, "pr_assign_points: need 1 <= dim <= 4096");
+    if (metric != PR_SQEUCLIDEAN && metric != PR_EUCLIDEAN)
+        return fail(PR_ERR_INVALID, "pr_assign_points: bad metric");
+    CostSource src;
+    src.XA = XA;
+    src.XB = XB;
+    src.dim = dim;
+    src.squared = metric == PR_SQEUCLIDEAN ? 1 : 0;
+    src.points = true;
+    return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
+                         ws_bytes, stream, "pr_assign_points");
 }
 
 // ---------------------------------------------------------------------------
@@ -1384,6 +1536,10 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
-    return launch_solve(p, C, dt, ldc, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, false,
+    CostSource src;
+    src.C = C;
+    src.dt = dt;
+    src.ldc = ldc;
+    return launch_solve(p, src, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, false,
                         "pr_assign_noalloc", st);
 }

@@ -24,6 +24,7 @@
 #include "prot_internal.cuh"
 #include "scan_common.cuh"
 #include "quantise.cuh"
+#include "points.cuh"
 
 namespace prot {
 namespace {
@@ -154,30 +155,8 @@ __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Costs from points.  d(b,a) = sum_k (xb_k - xa_k)^2 in FP32, one IEEE
-// operation at a time in ascending k (no contraction); Euclidean takes the
-// IEEE square root.  c = RN32(d / max d) so the largest cost is 1 (Sec. 1).
+// Costs from points (points.cuh): c = RN32(d / max d) per problem.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float dist_f32(const float *xb, const float *xa, int dim, int squared) {
-    float acc = 0.0f;
-    for (int k = 0; k < dim; ++k) {
-        const float t = __fsub_rn(xb[k], xa[k]);
-        const float sq = __fmul_rn(t, t);
-        acc = k == 0 ? sq : __fadd_rn(acc, sq);
-    }
-    return squared ? acc : __fsqrt_rn(acc);
-}
-
-__device__ __forceinline__ double dist_f64(const float *xb, const float *xa, int dim, int squared) {
-    double acc = 0.0;
-    for (int k = 0; k < dim; ++k) {
-        const double t = __dsub_rn((double)xb[k], (double)xa[k]);
-        const double sq = __dmul_rn(t, t);
-        acc = k == 0 ? sq : __dadd_rn(acc, sq);
-    }
-    return squared ? acc : __dsqrt_rn(acc);
-}
-
 __global__ void k_bpoints_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
                               int squared, const BDesc *__restrict__ d, int P,
                               long long total_groups, unsigned *maxbits) {
