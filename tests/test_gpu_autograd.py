@@ -93,3 +93,29 @@ def test_backward_kernel_at_exact_optimum_matches_finite_differences(prot):
             Xm[i, k] -= h
             fd = (loss(Xp, Y64) - loss(Xm, Y64)) / (2 * h)
             assert abs(fd - float(gX[0, i, k])) < 1e-4 * max(1.0, abs(fd))
+
+
+def test_config_sized_loss_sampled(prot):
+    """The bench's differentiable-loss workload (64 pairs, n = 4096, d = 3,
+    N(0,1) coordinates, squared Euclidean, eps = 0.01) in one batched
+    forward + backward: four sampled pairs match the oracle's plan, loss and
+    gradients bit for bit, and every pair's gradients obey grad_Y[sigma(i)] =
+    -grad_X[i]."""
+    import torch
+    B, n, d, eps = 64, 4096, 3, 0.01
+    X, Y = W.cloud_pairs_normal(B, n, d, seed=0)
+    Xt = torch.from_numpy(X).cuda().requires_grad_(True)
+    Yt = torch.from_numpy(Y).cuda().requires_grad_(True)
+    loss = prot.assignment_loss(Xt, Yt, eps)
+    loss.sum().backward()
+    rng = np.random.default_rng(1)
+    for p in sorted(rng.choice(B, size=4, replace=False).tolist()):
+        ref = OP.assign_points(Y[p], X[p], eps, squared=True)
+        assert abs(float(loss[p].detach()) - np.float32(ref["cost"] / n)) <= 1e-6 * abs(ref["cost"] / n)
+        gX, gY = OP.sqeuclid_backward(X[p], Y[p], ref["row_to_col"], 1.0)
+        assert np.array_equal(Xt.grad[p].cpu().numpy(), gX)
+        assert np.array_equal(Yt.grad[p].cpu().numpy(), gY)
+    res = prot.assign_batched_points(Yt.detach().reshape(-1, d), Xt.detach().reshape(-1, d), [n] * B, eps)
+    r2c = res["row_to_col"].reshape(B, n).long()
+    for p in range(B):
+        assert torch.equal(Yt.grad[p][r2c[p]], -Xt.grad[p])
