@@ -382,7 +382,33 @@ def run_extras(a, torch, prot, W, dev, stream):
     del costs
 
     ex["ot"] = run_ot(a, torch, prot, W, dev, reps=3)
+    ex["mnist_shaped"] = run_mnist_shaped(a, torch, prot, W, dev, stream)
     return ex
+
+
+def run_mnist_shaped(a, torch, prot, W, dev, stream):
+    """The paper's MNIST experiment on seeded MNIST-shaped images (the
+    dataset is not available): n unit-mass 28x28 images per side, L1 cost
+    divided by its maximum, eps in {0.75, 0.5, 0.25, 0.1}.  The cost matrix is
+    input preparation (torch.cdist on the device, FP32, then FP64 / max);
+    each eps is timed over 10 solves."""
+    A, B = W.mnist_shaped_pair(a.n, 3)
+    At = torch.from_numpy(A).to(dev, dtype=torch.float32)
+    Bt = torch.from_numpy(B).to(dev, dtype=torch.float32)
+    C = torch.cdist(Bt, At, p=1).to(torch.float64)
+    C /= C.max()
+    del At, Bt
+    ws = prot.Workspace(dev)
+    res = {"workload": f"{a.n} + {a.n} MNIST-shaped 28x28 unit-mass images (seeded strokes), "
+                       "L1 cost / max"}
+    for eps in (0.75, 0.5, 0.25, 0.1):
+        r = prot.assign(C, eps, ws=ws)
+        out = {k: v for k, v in r.items() if k != "stats"}
+        ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out), 10)
+        res[str(eps)] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+                         "cost_per_image": float(r["cost"].cpu()) / a.n}
+    del C
+    return res
 
 
 def run_ot(a, torch, prot, W, dev, reps):

@@ -120,3 +120,54 @@ def cloud_pairs_normal(batch: int, n: int, dim: int, seed: int):
     X = g.standard_normal((batch, n, dim), dtype=np.float64).astype(np.float32)
     Y = g.standard_normal((batch, n, dim), dtype=np.float64).astype(np.float32)
     return X, Y
+
+
+# -------------------------------------------------------------------------
+# MNIST-shaped synthetic images (the dataset itself is not available): the
+# paper's second experiment matches n = 10,000 28x28 gray-level digit images
+# of A against n of B, each normalised to unit mass, under the L1 distance
+# (at most 2), for eps in {0.75, 0.5, 0.25, 0.1}.
+# -------------------------------------------------------------------------
+
+def mnist_shaped(n: int, seed: int, strokes=(1, 3), samples: int = 40, sigma: float = 0.9,
+                 chunk: int = 256) -> np.ndarray:
+    """n seeded 28x28 stroke images, flattened to (n, 784) FP64, each
+    summing to 1.  An image is 1..3 quadratic Bezier strokes with control
+    points in the central 20x20 box, drawn by a Gaussian brush of width
+    sigma at `samples` points per stroke, clipped to [0, 1] gray levels with
+    faint pixels set to 0 (about a fifth of the pixels are lit, as in
+    handwritten digits)."""
+    g = rng(seed)
+    ns = g.integers(strokes[0], strokes[1] + 1, size=n)
+    ctrl = g.uniform(4.0, 24.0, size=(n, strokes[1], 3, 2))
+    t = np.linspace(0.0, 1.0, samples)[:, None]
+    grid = np.arange(28.0)
+    out = np.empty((n, 784))
+    for i0 in range(0, n, chunk):
+        c = ctrl[i0:i0 + chunk]                                       # (m, S, 3, 2)
+        p0, p1, p2 = c[:, :, 0, None, :], c[:, :, 1, None, :], c[:, :, 2, None, :]
+        pts = (1 - t) ** 2 * p0 + 2 * (1 - t) * t * p1 + t ** 2 * p2  # (m, S, samples, 2)
+        lit = (np.arange(strokes[1])[None, :] < ns[i0:i0 + chunk, None]).astype(np.float64)
+        # the brush is separable: exp(-(dy^2 + dx^2) / 2 s^2) = gy * gx
+        gy = np.exp(-(pts[..., 0, None] - grid) ** 2 / (2 * sigma * sigma)) * lit[:, :, None, None]
+        gx = np.exp(-(pts[..., 1, None] - grid) ** 2 / (2 * sigma * sigma))
+        img = np.einsum("msti,mstj->mij", gy, gx).reshape(c.shape[0], 784)
+        img = np.clip(img, 0.0, 1.0)
+        img[img < 0.1] = 0.0
+        out[i0:i0 + chunk] = img
+    return out / out.sum(axis=1, keepdims=True)
+
+
+def l1_cost(A: np.ndarray, B: np.ndarray, block: int = 32) -> np.ndarray:
+    """C[b, a] = sum_k |B[b, k] - A[a, k]| in FP64 (numpy order), divided by
+    the matrix maximum so that the largest cost is 1 (Sec. 1)."""
+    C = np.empty((B.shape[0], A.shape[0]))
+    for b0 in range(0, B.shape[0], block):
+        C[b0:b0 + block] = np.abs(B[b0:b0 + block, None, :] - A[None, :, :]).sum(-1)
+    m = C.max()
+    return C / m if m > 0 else C
+
+
+def mnist_shaped_pair(n: int, seed: int):
+    """A then B, n images each: (A, B) as (n, 784) FP64 unit-mass rows."""
+    return mnist_shaped(n, seed), mnist_shaped(n, seed + 7919)

@@ -315,3 +315,18 @@ def test_byte_test_forms_at_their_limits(prot, K):
     got = gpu_solve(prot, C, eps)
     assert_parity(got, oracle.assign(C, eps))
     assert_cells(got, C, eps)
+
+
+@pytest.mark.parametrize("eps", [0.75, 0.5, 0.25, 0.1])
+def test_mnist_shaped_workload(prot, eps):
+    """The paper's second experiment on seeded MNIST-shaped images (the
+    dataset is not available): unit-mass 28x28 images, L1 cost / max, the
+    paper's eps values; parity with the oracle and the Lemma 3.1 bound
+    against the exact optimum."""
+    A, B = W.mnist_shaped_pair(500, 11)
+    C = W.l1_cost(A, B)
+    got = gpu_solve(prot, C, eps)
+    ref = oracle.assign(C, eps)
+    assert_parity(got, ref)
+    opt, _ = oracle.hungarian(C)
+    assert opt - 1e-9 <= got["cost"] <= opt + 3 * eps * 500 + 1e-9
