@@ -278,14 +278,18 @@ def run_extras(a, torch, prot, W, dev, stream):
     C = torch.from_numpy(W.assignment_euclid_2d(a.n, a.seed)).to(dev)
     ws = prot.Workspace(dev)
     sweep = {}
-    for eps in (0.1, 0.005):
-        r = prot.assign(C, eps, ws=ws)
-        out = {k: v for k, v in r.items() if k != "stats"}
-        prot.assign(C, eps, ws=ws, sync=False, out=out)
-        ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out), 10)
-        sweep[str(eps)] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
-                           "cells_examined": r["stats"]["cells_examined"],
-                           "bytes_scanned": r["stats"]["bytes_scanned"]}
+    for eps in (0.1, 0.01, 0.005):
+        for rule in ("lowest", "offset"):
+            if rule == "lowest" and eps == a.eps:
+                continue  # the headline line itself
+            r = prot.assign(C, eps, ws=ws, rule=rule)
+            out = {k: v for k, v in r.items() if k != "stats"}
+            prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule)
+            ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), 10)
+            key = str(eps) if rule == "lowest" else f"{eps} offset rule"
+            sweep[key] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+                          "cells_examined": r["stats"]["cells_examined"],
+                          "bytes_scanned": r["stats"]["bytes_scanned"]}
     ex["assign_eps_sweep"] = sweep
     del C
     # the same workload with the costs formed on the device from the points
@@ -402,11 +406,13 @@ def run_mnist_shaped(a, torch, prot, W, dev, stream):
     res = {"workload": f"{a.n} + {a.n} MNIST-shaped 28x28 unit-mass images (seeded strokes), "
                        "L1 cost / max"}
     for eps in (0.75, 0.5, 0.25, 0.1):
-        r = prot.assign(C, eps, ws=ws)
-        out = {k: v for k, v in r.items() if k != "stats"}
-        ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out), 10)
-        res[str(eps)] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
-                         "cost_per_image": float(r["cost"].cpu()) / a.n}
+        for rule in ("lowest", "offset"):
+            r = prot.assign(C, eps, ws=ws, rule=rule)
+            out = {k: v for k, v in r.items() if k != "stats"}
+            ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), 10)
+            res[str(eps) if rule == "lowest" else f"{eps} offset rule"] = {
+                "ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
+                "cost_per_image": float(r["cost"].cpu()) / a.n}
     del C
     return res
 

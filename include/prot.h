@@ -104,6 +104,29 @@ pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int
                     void *stream);
 
 /*
+ * pr_assign_rule -- pr_assign with a choice of the maximal matching of step
+ * (I).  Sec. 2.2 accepts any maximal matching of the admissible graph on the
+ * free vertices (the greedy of Lemma 3.4, or Israeli-Itai's randomized one
+ * for the parallel bound); every bound of Sec. 2.1 and 3 holds for each.
+ *   PR_RULE_LOWEST  pr_assign's rule: every free row proposes to its
+ *                   lowest-index admissible column not taken in an earlier
+ *                   round of the phase, each column takes its lowest proposer.
+ *   PR_RULE_OFFSET  the same rounds, but in phase p (counted from 1) row b
+ *                   scans cyclically from column splitmix64(p << 32 | b) mod
+ *                   n_cols (SplitMix64's output function, Steele, Lea and
+ *                   Flood 2014) and stops after one full turn.  Spreading the
+ *                   first proposals over the columns cuts the rounds of a
+ *                   phase where most edges are admissible (large eps).
+ * Other arguments, outputs and errors as pr_assign; cells_examined counts
+ * the columns each scan passes.
+ */
+typedef enum { PR_RULE_LOWEST = 0, PR_RULE_OFFSET = 1 } pr_rule;
+pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                         int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
+                         int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/*
  * pr_dual_bound -- the a-posteriori certificate of a pr_assign solve
  * (Lemma 3.1).  The duals it returns satisfy Eq. (2), y(a) + y(b) <= cbar +
  * eps on every edge; summed over any matching that covers the rows (column

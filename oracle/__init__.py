@@ -34,6 +34,7 @@ MODE_CHECK = 2
 MODE_REVERSE = 4
 MODE_SEQUENTIAL = 8
 MODE_EVICT_RESUME = 16
+MODE_OFFSET = 32
 
 
 class Stats(ctypes.Structure):

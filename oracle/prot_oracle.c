@@ -137,6 +137,17 @@ int64_t or_check_state(const int32_t *cb, int32_t nB, int32_t nA,
     return bad;
 }
 
+/* SplitMix64's output function (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014): the seeded start columns
+ * of OR_MODE_OFFSET are splitmix64(phase << 32 | b) mod |A|. */
+static uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
 /*
  * One run of the main routine of Sec. 2.2 on integer costs cb (row-major,
  * nB x nA, nB <= nA).  Outputs the matching before completion and both dual
@@ -162,9 +173,11 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
     int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nA);
     int32_t *mround = (int32_t *)malloc(sizeof(int32_t) * nB);
     int32_t *resume = (int32_t *)calloc((size_t)nB, sizeof(int32_t));
-    if (!F || !act || !nxt || !mate || !ptr || !prop || !taken || !best || !mround || !resume) {
+    int32_t *covered = (int32_t *)calloc((size_t)nB, sizeof(int32_t));  /* OR_MODE_OFFSET */
+    if (!F || !act || !nxt || !mate || !ptr || !prop || !taken || !best || !mround || !resume ||
+        !covered) {
         free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
-        free(taken); free(best); free(mround); free(resume);
+        free(taken); free(best); free(mround); free(resume); free(covered);
         return OR_ERR_NOMEM;
     }
     memset(st, 0, sizeof(*st));
@@ -204,6 +217,10 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
              * same proposals. */
             if (mode & OR_MODE_EVICT_RESUME) ptr[b] = resume[b];
             resume[b] = 0;
+            if (mode & OR_MODE_OFFSET) {
+                ptr[b] = (int32_t)(splitmix64(((uint64_t)st->phases << 32) | (uint32_t)b) % (uint64_t)nA);
+                covered[b] = 0;
+            }
         }
         int32_t nact = nf;
         for (int32_t i = 0; i < nf; ++i) act[i] = F[i];
@@ -238,6 +255,18 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
                     int32_t b = act[i];
                     int32_t start = (mode & OR_MODE_LITERAL) ? 0 : ptr[b];
                     int32_t p = -1;
+                    if (mode & OR_MODE_OFFSET) {
+                        /* cyclic scan from the row's start column; a loser
+                         * goes on after the column it lost, until every
+                         * column has been seen once in this phase */
+                        while (covered[b] < nA) {
+                            int32_t a = ptr[b];
+                            ptr[b] = (a + 1 == nA) ? 0 : a + 1;
+                            covered[b] += 1;
+                            st->scanned += 1;
+                            if (taken[a] == 0 && admissible(cb, nA, y_b, y_a, b, a)) { p = a; break; }
+                        }
+                    } else
                     for (int32_t a = start; a < nA; ++a) {
                         st->scanned += 1;
                         if (taken[a] == 0 && admissible(cb, nA, y_b, y_a, b, a)) { p = a; break; }
@@ -261,7 +290,7 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
                     if (best[p] == b) {
                         mate[b] = p; mround[b] = r;
                     } else {
-                        ptr[b] = p + 1;               /* resume after p */
+                        if (!(mode & OR_MODE_OFFSET)) ptr[b] = p + 1;  /* resume after p */
                         nxt[nn++] = b;
                     }
                 }
@@ -306,7 +335,7 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
     }
 
     free(F); free(act); free(nxt); free(mate); free(ptr); free(prop);
-    free(taken); free(best); free(mround); free(resume);
+    free(taken); free(best); free(mround); free(resume); free(covered);
     return rc;
 }
 

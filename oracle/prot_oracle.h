@@ -17,6 +17,9 @@
 #define OR_MODE_CHECK 2       /* check (I1)/(I2) after every phase          */
 #define OR_MODE_REVERSE 4     /* process B' in descending order             */
 #define OR_MODE_SEQUENTIAL 8  /* the paper's sequential greedy (Lemma 3.4)  */
+#define OR_MODE_OFFSET 32   /* step I rule with seeded start columns: in phase
+                               p every free row b scans cyclically from
+                               column splitmix64(p << 32 | b) mod |A|        */
 #define OR_MODE_EVICT_RESUME 16 /* a row evicted in phase p starts its scan in
                                    phase p+1 after the column it lost (same
                                    results; fewer entries examined)         */

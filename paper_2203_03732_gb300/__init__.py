@@ -61,7 +61,8 @@ def _stream_handle(torch, device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out=None):
+def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out=None,
+           rule: str = "lowest"):
     """Additive eps-approximate assignment (Sec. 2.2 of the paper).
 
     C: (n_rows, n_cols) float32/float64 tensor with costs in [0, 1],
@@ -70,6 +71,8 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
        copied back (the end-to-end path).
     Returns a dict: row_to_col, col_to_row (int32), y_row, y_col (int32 duals
     in units of eps), cost (float64 scalar tensor) and, when sync, stats.
+    rule: the maximal matching of step (I), "lowest" (lowest-index columns)
+    or "offset" (seeded start columns per row and phase); see pr_assign_rule.
     """
     torch = _torch()
     L = _lib.load()
@@ -103,11 +106,17 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
             cost=torch.empty((), dtype=torch.float64, device=dev),
         )
     st = _lib.PrStats()
-    rc = L.pr_assign(Cd.data_ptr(), dt, Cd.stride(0), nB, nA, float(eps),
-                     out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
-                     out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["cost"].data_ptr(),
-                     ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
-                     _stream_handle(torch, dev))
+    args = (Cd.data_ptr(), dt, Cd.stride(0), nB, nA, float(eps),
+            out["row_to_col"].data_ptr(), out["col_to_row"].data_ptr(),
+            out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["cost"].data_ptr(),
+            ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
+            _stream_handle(torch, dev))
+    if rule == "lowest":
+        rc = L.pr_assign(*args)
+    elif rule == "offset":
+        rc = L.pr_assign_rule(_lib.PR_RULE_OFFSET, *args)
+    else:
+        raise ValueError("rule must be 'lowest' or 'offset'")
     _lib.check(rc, "pr_assign")
     res = dict(out)
     if sync:

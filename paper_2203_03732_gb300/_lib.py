@@ -45,6 +45,9 @@ class PrBatchedTune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
+PR_RULE_LOWEST = 0
+PR_RULE_OFFSET = 1
+
 PR_SQEUCLIDEAN = 0
 PR_EUCLIDEAN = 1
 
@@ -87,6 +90,8 @@ SIGNATURES = {
                                                   ctypes.POINTER(PrBatchedTune), ctypes.POINTER(ctypes.c_float),
                                                   _vp, _sz, _vp]),
     "pr_dual_bound": (ctypes.c_int, [_vp, _vp, _i32, _i32, _dbl, _vp, _vp, _vp]),
+    "pr_assign_rule": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp,
+                                      _vp, _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_assign_points": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                         _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),

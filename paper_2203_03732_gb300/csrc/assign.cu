@@ -144,7 +144,20 @@ struct Params {
     int profile;
     int nslots;        // cluster mode: row slots in shared memory (one per scanning warp)
     int slot_bytes;    // bytes per row slot (a whole cbar row, 128-byte multiple)
+    int rule = 0;      // step I: 0 lowest-index columns, 1 seeded start columns (PR_RULE_OFFSET)
 };
+
+// PR_RULE_OFFSET: in phase `phase1` (counted from 1) free row b starts its
+// scan at column splitmix64(phase1 << 32 | b) mod n_A and goes round the row
+// once.  SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ int phase_offset(long long phase1, int b, int nA) {
+    unsigned long long x = ((unsigned long long)phase1 << 32) | (unsigned)b;
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (int)(x % (unsigned long long)nA);
+}
 
 // ---------------------------------------------------------------------------
 // k_init
@@ -197,9 +210,11 @@ template <class CB, bool F7>
 // tgt_in < 0: the row's y(b) is not known yet (an evicted row); lane 0 reads
 // it after the row loads are issued, so the two reads overlap.  The target
 // used comes back in tgt_out.
+// Columns >= stop are not candidates; loads stop at lim (stop rounded up to
+// a whole load, <= ldq).
 __device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const CB *ks,
                                                const unsigned *tk, bool check_taken, int c0,
-                                               int start, int ldq, int tgt_in, const int *yb,
+                                               int start, int ldq, int stop, int tgt_in, const int *yb,
                                                int &tgt_out, int lane) {
     constexpr int W = kPerLoad<CB>;
     constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
@@ -223,6 +238,8 @@ __device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const
         }
         const int lo = start - idx;
         if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
+        const int hi = stop - idx;
+        if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
         if (check_taken && m) {
             // the W columns idx .. idx + W - 1 lie in one 32-bit word of the bitmap
             m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
@@ -242,9 +259,11 @@ __device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const
 // ---------------------------------------------------------------------------
 struct Smem {
     int2 fl[2][kKeepMax];     // kept rows of this phase / next phase, as pool entries
-    int4 ql[2][kListSm];      // (b, a, y(b)) proposals of this round / previous round
+    int4 ql[2][kListSm];      // (b, a, y(b), origin) proposals of this round / previous round
     int job_b[kBatch];
     int job_start[kBatch];
+    int job_stop[kBatch];     // the scan covers columns [start, stop)
+    int job_pair[kBatch];     // -1; or the job scanning the row's wrapped part [0, origin); -2 for that job
     int job_tgt[kBatch];
     int job_best[kBatch];
     int2 don[kBatch];         // pool entries given to the pool in this batch
@@ -266,10 +285,10 @@ struct Lists {
     int4 *ql[2];  // global overflow of ql
 };
 
-__device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a, int y) {
+__device__ __forceinline__ void ql_push(Smem &s, const Lists &g, int which, int b, int a, int y, int org) {
     const int i = atomicAdd(&s.nql[which], 1);
-    if (i < kListSm) s.ql[which][i] = make_int4(b, a, y, 0);
-    else g.ql[which][i - kListSm] = make_int4(b, a, y, 0);
+    if (i < kListSm) s.ql[which][i] = make_int4(b, a, y, org);
+    else g.ql[which][i - kListSm] = make_int4(b, a, y, org);
 }
 __device__ __forceinline__ int4 ql_get(const Smem &s, const Lists &g, int which, int i) {
     return i < kListSm ? s.ql[which][i] : g.ql[which][i - kListSm];
@@ -424,13 +443,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned par
     }
 }
 
-// Lowest candidate column >= start in the slot holding cbar[s_al .. ldq) of
-// one row (the test of warp_scan_chunk), or -1.  Four 16-byte shared loads
+// Lowest candidate column in [start, stop) in the slot holding cbar[s_al ..
+// ldq) of one row, ldq here being the end of the copy (the test of
+// warp_scan_chunk), or -1.  Four 16-byte shared loads
 // per lane are in flight per step.
 template <class CB, bool F7>
 __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const CB *ks, const unsigned *tk,
-                                              bool check_taken, int s_al, int start, int ldq, uint32_t tgt,
-                                              int lane) {
+                                              bool check_taken, int s_al, int start, int ldq, int stop,
+                                              uint32_t tgt, int lane) {
     constexpr int W = kPerLoad<CB>;
     constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
     constexpr int kU = 4;
@@ -453,6 +473,8 @@ __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const C
             }
             const int lo = start - idx;
             if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
+            const int hi = stop - idx;
+            if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
             if (check_taken && m) m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
             const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
             if (any == 0) continue;
@@ -502,18 +524,20 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
             for (int j = warp; j < nq; j += p.nslots) {
                 const int b = s.job_b[j];
                 const int start = s.job_start[j];
+                const int stop = s.job_stop[j];
+                const int lim = (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1);
                 const int s_al = start & ~(kPerLoad<CB> - 1);
                 const uint32_t tgt = (uint32_t)s.job_tgt[j];
                 int a = -1;
-                if (s_al < p.ldq && !(mstate & 2u)) {
-                    const unsigned bytes = (unsigned)((p.ldq - s_al) * sizeof(CB));
+                if (s_al < lim && !(mstate & 2u)) {
+                    const unsigned bytes = (unsigned)((lim - s_al) * sizeof(CB));
                     const CB *src = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq + s_al;
                     __syncwarp();
                     if (lane == 0) bulk_row_copy(slot, src, bytes, &s.mbar[warp]);
                     if (mbar_wait(&s.mbar[warp], mstate & 1u, kCopyWaitCycles)) {
                         mstate ^= 1u;
                         my_bytes += bytes;
-                        a = warp_scan_slot<CB, F7>(slot, ks, tk, R > Rps, s_al, start, p.ldq, tgt, lane);
+                        a = warp_scan_slot<CB, F7>(slot, ks, tk, R > Rps, s_al, start, lim, stop, tgt, lane);
                     } else {
                         mstate |= 2u;
                         if (lane == 0) record_error(&p.ctl->head, PR_ERR_TIMEOUT);
@@ -533,18 +557,20 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (slot < ng) {
             const int b = s.job_b[g0 + slot];
             const int start = s.job_start[g0 + slot];
+            const int stop = s.job_stop[g0 + slot];
+            const int lim = (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1);
             const int s_al = start & ~(kPerLoad<CB> - 1);
             int tgt = s.job_tgt[g0 + slot];
             const CB *row = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq;
             volatile int *vbest = &s.best[slot];
             const bool known = tgt >= 0;
-            for (int c0 = s_al + sub * kChunk<CB>; c0 < p.ldq; c0 += warps_per_row * kChunk<CB>) {
+            for (int c0 = s_al + sub * kChunk<CB>; c0 < lim; c0 += warps_per_row * kChunk<CB>) {
                 // warp-uniform early exit: lane 0's view of the row's best so far
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
-                my_bytes += sizeof(CB) * (unsigned long long)min(kChunk<CB>, p.ldq - c0);
+                my_bytes += sizeof(CB) * (unsigned long long)min(kChunk<CB>, lim - c0);
                 int t_used;
-                const int a = warp_scan_chunk<CB, F7>(row, ks, tk, R > Rps, c0, start, p.ldq, tgt, p.y_b + b,
-                                                  t_used, lane);
+                const int a = warp_scan_chunk<CB, F7>(row, ks, tk, R > Rps, c0, start, lim, stop, tgt,
+                                                      p.y_b + b, t_used, lane);
                 tgt = t_used;
                 if (a >= 0) {
                     if (lane == 0) atomicMin(&s.best[slot], a);
@@ -562,11 +588,26 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
     __syncthreads();
     const unsigned long long tB = p.profile ? ptimer() : 0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+        const int pair = s.job_pair[j];
+        if (pair == -2) continue;  // a row's wrapped part: decided with the row's first job
         const int b = s.job_b[j];
-        const int a = s.job_best[j];
-        const int st = s.job_start[j];
-        // entries examined: start .. a, or start .. the row's end
-        cells += a != 0x7FFFFFFF ? (unsigned)(a - st + 1) : (st < p.nA ? (unsigned)(p.nA - st) : 0u);
+        int a = s.job_best[j];
+        const int st = s.job_start[j], sp = s.job_stop[j];
+        // entries examined: start .. a, or the whole range [start, stop)
+        unsigned ex = a != 0x7FFFFFFF ? (unsigned)(a - st + 1) : (st < sp ? (unsigned)(sp - st) : 0u);
+        int org = 0;  // PR_RULE_OFFSET: the row's first column in this phase
+        if (pair >= 0) {
+            const int a2 = s.job_best[pair];
+            const int sp2 = s.job_stop[pair];  // the wrapped part is [0, org)
+            if (a == 0x7FFFFFFF) {
+                a = a2;
+                ex += a2 != 0x7FFFFFFF ? (unsigned)(a2 + 1) : (unsigned)sp2;
+            }
+            org = sp2;
+        } else if (p.rule) {
+            org = sp == p.nA ? 0 : sp;
+        }
+        cells += ex;
         if (a != 0x7FFFFFFF) {
             const unsigned long long old = atomicMax(p.prop + a, word_of(R, b));
             const unsigned t = tag_of(old);
@@ -590,7 +631,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
             } else {
                 record_error(&p.ctl->head, PR_ERR_INTERNAL);
             }
-            ql_push(s, g, qcur, b, a, s.job_tgt[j] + 1);
+            ql_push(s, g, qcur, b, a, s.job_tgt[j] + 1, org);
             s.had_prop = 1;
         } else {
             atomicAdd(p.y_b + b, 1);  // step (III b): free w.r.t. M' -> relabel
@@ -778,12 +819,15 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             __syncthreads();
             const unsigned long long t_r1 = p.profile ? ptimer() : 0;
             unsigned long long t_mark = t_r1;
-            for (int i0 = 0; i0 < nitems; i0 += kBatch) {
-                const int cnt = min(kBatch, nitems - i0);
+            // PR_RULE_OFFSET turns a row into up to two jobs: half as many per batch
+            const int per_batch = p.rule ? kBatch / 2 : kBatch;
+            for (int i0 = 0; i0 < nitems; i0 += per_batch) {
+                const int cnt = min(per_batch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                     const int it = i0 + i;
                     const bool pre = i0 == 0 && i == (int)threadIdx.x;  // loaded above
-                    int b, y = -1, start = 0;
+                    // the row's scan covers [start, stop), then [0, wrap) if wrap > 0
+                    int b, y = -1, start = 0, stop = p.nA, wrap = 0;
                     if (first_round) {
                         if (phase == 0) {
                             b = cta + it * (int)G;
@@ -801,6 +845,10 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                             start = -1 - y;
                             y = -1;
                         }
+                        if (p.rule) {  // once round the row from its seeded first column
+                            start = phase_offset(phase + 1, b, p.nA);
+                            wrap = start;
+                        }
                     } else {
                         const int4 q = pre ? pre_q : ql_get(s, g, qcur ^ 1, it);
                         const unsigned long long w = pre ? pre_word : ld_relaxed_u64(p.prop + q.y);
@@ -808,11 +856,28 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                         if (row_of(w) == b) continue;  // won: matched, leaves B'
                         start = q.y + 1;               // lost: resume after a
                         y = q.z;
+                        // PR_RULE_OFFSET (first column q.w): before the wrap the rest
+                        // of the row and then [0, q.w); after it, up to q.w
+                        if (q.w > 0) {
+                            if (q.y >= q.w) wrap = q.w;
+                            else stop = q.w;
+                        }
                     }
-                    const int j = atomicAdd(&s.njob, 1);
+                    const int tg = y >= 0 ? y - 1 : -1;
+                    const int nj = wrap > 0 ? 2 : 1;
+                    const int j = atomicAdd(&s.njob, nj);
                     s.job_b[j] = b;
                     s.job_start[j] = start;
-                    s.job_tgt[j] = y >= 0 ? y - 1 : -1;
+                    s.job_stop[j] = stop;
+                    s.job_tgt[j] = tg;
+                    s.job_pair[j] = nj == 2 ? j + 1 : -1;
+                    if (nj == 2) {
+                        s.job_b[j + 1] = b;
+                        s.job_start[j + 1] = 0;
+                        s.job_stop[j + 1] = wrap;
+                        s.job_tgt[j + 1] = tg;
+                        s.job_pair[j + 1] = -2;
+                    }
                 }
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += ptimer() - t_mark;
@@ -1359,7 +1424,7 @@ namespace {
 pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, double eps,
                         int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row, int32_t *y_col,
                         double *cost, pr_stats *stats, void *ws, size_t ws_bytes, void *stream,
-                        const char *who) {
+                        const char *who, int rule = PR_RULE_LOWEST) {
     if (!row_to_col || !col_to_row || !y_row || !y_col || !cost)
         return fail(PR_ERR_INVALID, "%s: NULL pointer argument", who);
     if (n_rows < 1 || n_cols < n_rows || n_cols > (1 << 24) - 1)
@@ -1393,6 +1458,7 @@ pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, d
     p.nB = n_rows;
     p.nA = n_cols;
     p.ldq = L.ldq;
+    p.rule = rule;
     return launch_solve(p, src, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, true, who, st);
 }
 
@@ -1412,6 +1478,22 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     src.ldc = ldc;
     return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
                          ws_bytes, stream, "pr_assign");
+}
+
+extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                                    int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
+                                    int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
+                                    size_t ws_bytes, void *stream) {
+    if (rule != PR_RULE_LOWEST && rule != PR_RULE_OFFSET) return fail(PR_ERR_INVALID, "pr_assign_rule: bad rule");
+    if (!C) return fail(PR_ERR_INVALID, "pr_assign_rule: NULL pointer argument");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_rule: bad dtype");
+    if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_rule: ldc < n_cols");
+    CostSource src;
+    src.C = C;
+    src.dt = dt;
+    src.ldc = ldc;
+    return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
+                         ws_bytes, stream, "pr_assign_rule", (int)rule);
 }
 
 extern "C" pr_status pr_assign_points(const float *XA, const float *XB, int32_t dim, pr_metric metric,

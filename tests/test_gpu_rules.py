@@ -1,0 +1,91 @@
+"""GPU parity of the seeded-start-column rule of step (I) (pr_assign_rule
+with PR_RULE_OFFSET) against the oracle's OR_MODE_OFFSET: bit-exact
+matching, both dual vectors, phase and round counts, and the exact number of
+cost entries the scans pass, in every phase-loop form."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_03732_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["grid", "grid-slots", "cluster"]
+
+
+@pytest.fixture(scope="module")
+def prot():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_03732_gb300 import build
+    build.build()
+    import paper_2203_03732_gb300 as P
+    return P
+
+
+def set_form(monkeypatch, form):
+    monkeypatch.setenv("PR_PHASE_MODE", "cluster" if form == "cluster" else "grid")
+    monkeypatch.setenv("PR_SCAN", "auto" if form == "grid-slots" else "regs")
+
+
+def check(prot, C, eps):
+    import torch
+    r = prot.assign(torch.from_numpy(C).cuda(), eps, rule="offset")
+    ref = oracle.assign(C, eps, mode=oracle.MODE_OFFSET)
+    for k in ("row_to_col", "col_to_row", "y_row", "y_col"):
+        assert np.array_equal(r[k].cpu().numpy(), ref[k]), k
+    for k in ("phases", "rounds", "free_at_stop"):
+        assert r["stats"][k] == ref["stats"][k], k
+    assert r["stats"]["cells_examined"] == ref["stats"]["scanned"]
+    assert abs(float(r["cost"]) - ref["cost"]) <= 1e-12 * max(abs(ref["cost"]), 1e-300)
+    return r, ref
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n,eps", [(64, 0.1), (1000, 0.01), (4097, 0.005), (5003, 0.1), (700, 0.002)])
+def test_offset_rule_parity(prot, monkeypatch, form, n, eps):
+    set_form(monkeypatch, form)
+    check(prot, W.assignment_euclid_2d(n, 90 + n), eps)
+
+
+def test_offset_rule_unbalanced(prot):
+    C = W.assignment_euclid_2d(900, 4, n_a=2300)
+    for eps in (0.1, 0.02):
+        check(prot, C, eps)
+
+
+def test_offset_rule_full_size(prot):
+    """n = 10,000 at eps = 0.1 (the paper's largest eps) with the offset rule."""
+    r, _ = check(prot, W.assignment_euclid_2d(10000, 0), 0.1)
+    low = oracle.assign(W.assignment_euclid_2d(10000, 0), 0.1)["stats"]
+    assert r["stats"]["rounds"] * 3 < low["rounds"]
+
+
+@pytest.mark.parametrize("eps", [0.75, 0.25])
+def test_offset_rule_mnist_shaped(prot, eps):
+    """Where most edges are admissible the rule needs far fewer rounds than
+    the lowest-index rule, with the same guarantees (Lemma 3.1 bound)."""
+    import torch
+    A, B = W.mnist_shaped_pair(600, 5)
+    C = W.l1_cost(A, B)
+    r, _ = check(prot, C, eps)
+    low = prot.assign(torch.from_numpy(C).cuda(), eps)
+    if eps == 0.75:
+        assert r["stats"]["rounds"] * 4 < low["stats"]["rounds"]
+    opt, _ = oracle.hungarian(C)
+    assert opt - 1e-9 <= float(r["cost"]) <= opt + 3 * eps * 600 + 1e-9
+
+
+def test_bad_rule(prot):
+    import ctypes
+    import torch
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load()
+    C = torch.rand(10, 10, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        prot.assign(C, 0.1, rule="random")
+    st = _lib.PrStats()
+    rc = L.pr_assign_rule(7, C.data_ptr(), 1, 10, 10, 10, 0.1, None, None, None, None, None,
+                          ctypes.byref(st), None, 0, None)
+    assert rc == _lib.PR_ERR_INVALID

@@ -362,3 +362,110 @@ def test_float32_input_widened_exactly():
     r64 = oracle.assign(C.astype(np.float64), 0.05)
     assert np.array_equal(r32["row_to_col"], r64["row_to_col"])
     assert r32["cost"] == r64["cost"]
+
+
+# -------------------------------------------------------------------------
+# Another step I rule: seeded start columns (OR_MODE_OFFSET)
+# -------------------------------------------------------------------------
+
+def _splitmix64(x):
+    """SplitMix64's output function (Steele, Lea, Flood, OOPSLA 2014)."""
+    M = (1 << 64) - 1
+    x = (x + 0x9E3779B97F4A7C15) & M
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M
+    return x ^ (x >> 31)
+
+
+def _offset_rule_literal(cb, T):
+    """Sec. 2.2 with the offset rule, written out in Python: in phase p
+    every free b scans cyclically from column splitmix64(p << 32 | b) mod n_A
+    and proposes to the first admissible column not taken in an earlier
+    round; each column takes its lowest proposer; losers go on after the
+    column they lost until they have seen every column once."""
+    nB, nA = len(cb), len(cb[0])
+    yb, ya = [1] * nB, [0] * nA
+    mb, ma = [-1] * nB, [-1] * nA
+    phases = rounds = 0
+    while True:
+        F = [b for b in range(nB) if mb[b] < 0]
+        if len(F) <= T:
+            break
+        phases += 1
+        pos = {b: _splitmix64((phases << 32) | b) % nA for b in F}
+        seen = {b: 0 for b in F}
+        taken, mate, act = set(), {b: -1 for b in F}, list(F)
+        while True:
+            prop = {}
+            for b in act:
+                while seen[b] < nA:
+                    a = pos[b]
+                    pos[b] = (a + 1) % nA
+                    seen[b] += 1
+                    if a not in taken and ya[a] + yb[b] == cb[b][a] + 1:
+                        prop[b] = a
+                        break
+            if not prop:
+                break
+            rounds += 1
+            win = {}
+            for b, a in prop.items():
+                win[a] = min(win.get(a, nB), b)
+            act = [b for b, a in prop.items() if win[a] != b]
+            for a, b in win.items():
+                mate[b] = a
+                taken.add(a)
+            if not act:
+                break
+        for b in F:
+            a = mate[b]
+            if a >= 0:
+                if ma[a] >= 0:
+                    mb[ma[a]] = -1
+                ma[a], mb[b] = b, a
+        for b in F:
+            if mate[b] >= 0:
+                ya[mate[b]] -= 1
+            else:
+                yb[b] += 1
+    return mb, ma, yb, ya, phases, rounds
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_offset_rule_equals_literal_restatement(seed):
+    g = np.random.default_rng(seed)
+    n = int(g.integers(2, 9))
+    C = rand_costs(seed, n, n, "few" if seed % 2 else "uniform")
+    for eps in (0.5, 0.2, 0.1):
+        cb = oracle.quantise(C, eps)
+        T = oracle.threshold(eps, n)
+        r = oracle.assign_int(cb, T, mode=oracle.MODE_OFFSET)
+        mb, ma, yb, ya, ph, rd = _offset_rule_literal(cb.tolist(), T)
+        assert r["match_b"].tolist() == mb and r["match_a"].tolist() == ma
+        assert r["y_b"].tolist() == yb and r["y_a"].tolist() == ya
+        assert r["stats"]["phases"] == ph and r["stats"]["rounds"] == rd
+
+
+@pytest.mark.parametrize("n,eps,sq", [(60, 0.1, True), (150, 0.02, False), (300, 0.005, True)])
+def test_offset_rule_invariants_and_bound(n, eps, sq):
+    """Any maximal matching per phase keeps Lemma 2.1, (I1)/(I2) and the
+    3 eps n bound (Sec. 2.1); the offset rule is one."""
+    C = W.assignment_sq_euclid_2d(n, 3) if sq else W.assignment_euclid_2d(n, 3)
+    r = oracle.assign(C, eps, mode=oracle.MODE_OFFSET | oracle.MODE_CHECK)
+    assert r["stats"]["violations"] == 0
+    opt, _ = oracle.hungarian(C)
+    assert opt - 1e-12 <= r["cost"] <= opt + 3 * eps * n + 1e-12
+
+
+def test_offset_rule_breaks_the_round_convoy():
+    """Where most edges are admissible (large eps) the lowest-index rule
+    sends every loser to the same next columns and needs many rounds; start
+    columns spread the proposals.  Recorded on the MNIST-shaped workload."""
+    A, B = W.mnist_shaped_pair(400, 3)
+    C = W.l1_cost(A, B)
+    cb = oracle.quantise(C, 0.75)
+    T = oracle.threshold(0.75, 400)
+    low = oracle.assign_int(cb, T)["stats"]
+    off = oracle.assign_int(cb, T, mode=oracle.MODE_OFFSET)["stats"]
+    assert low["phases"] == off["phases"] == 1
+    assert off["rounds"] * 4 < low["rounds"]
