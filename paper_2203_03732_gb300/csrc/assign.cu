@@ -206,7 +206,7 @@ __device__ __forceinline__ uint4 widen_hi(uint4 x) {
 // in the phase's taken set tk (shared memory; empty in a phase's first
 // round), or -1.  Lane l covers kPerLoad<CB> consecutive columns of each of
 // the kUnroll loads, all issued before any is used.
-template <class CB, bool F7>
+template <class CB, bool F7, bool OFS>
 // tgt_in < 0: the row's y(b) is not known yet (an evicted row); lane 0 reads
 // it after the row loads are issued, so the two reads overlap.  The target
 // used comes back in tgt_out.
@@ -238,8 +238,10 @@ __device__ __forceinline__ int warp_scan_chunk(const CB *__restrict__ row, const
         }
         const int lo = start - idx;
         if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
-        const int hi = stop - idx;
-        if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
+        if (OFS) {  // a scan that ends before the row's end (PR_RULE_OFFSET)
+            const int hi = stop - idx;
+            if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
+        }
         if (check_taken && m) {
             // the W columns idx .. idx + W - 1 lie in one 32-bit word of the bitmap
             m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
@@ -447,7 +449,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, unsigned par
 // ldq) of one row, ldq here being the end of the copy (the test of
 // warp_scan_chunk), or -1.  Four 16-byte shared loads
 // per lane are in flight per step.
-template <class CB, bool F7>
+template <class CB, bool F7, bool OFS>
 __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const CB *ks, const unsigned *tk,
                                               bool check_taken, int s_al, int start, int ldq, int stop,
                                               uint32_t tgt, int lane) {
@@ -473,8 +475,10 @@ __device__ __forceinline__ int warp_scan_slot(const unsigned char *slot, const C
             }
             const int lo = start - idx;
             if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
-            const int hi = stop - idx;
-            if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
+            if (OFS) {
+                const int hi = stop - idx;
+                if (hi < W) m &= hi <= 0 ? 0u : kAll >> (W - hi);
+            }
             if (check_taken && m) m &= ~(tk[idx >> 5] >> (idx & 31)) & kAll;
             const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
             if (any == 0) continue;
@@ -494,7 +498,7 @@ constexpr long long kCopyWaitCycles = 2000000000ll;
 // with warps_per_row warps per row; cluster form: one row per warp through
 // its slot); then every proposal (atomicMax) or relabel at once; then the
 // pool donations.
-template <class CB, bool SL, bool F7>
+template <class CB, bool SL, bool F7, bool OFS>
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
@@ -524,8 +528,8 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
             for (int j = warp; j < nq; j += p.nslots) {
                 const int b = s.job_b[j];
                 const int start = s.job_start[j];
-                const int stop = s.job_stop[j];
-                const int lim = (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1);
+                const int stop = OFS ? s.job_stop[j] : p.nA;
+                const int lim = OFS ? (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1) : p.ldq;
                 const int s_al = start & ~(kPerLoad<CB> - 1);
                 const uint32_t tgt = (uint32_t)s.job_tgt[j];
                 int a = -1;
@@ -537,7 +541,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                     if (mbar_wait(&s.mbar[warp], mstate & 1u, kCopyWaitCycles)) {
                         mstate ^= 1u;
                         my_bytes += bytes;
-                        a = warp_scan_slot<CB, F7>(slot, ks, tk, R > Rps, s_al, start, lim, stop, tgt, lane);
+                        a = warp_scan_slot<CB, F7, OFS>(slot, ks, tk, R > Rps, s_al, start, lim, stop, tgt, lane);
                     } else {
                         mstate |= 2u;
                         if (lane == 0) record_error(&p.ctl->head, PR_ERR_TIMEOUT);
@@ -557,8 +561,8 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
         if (slot < ng) {
             const int b = s.job_b[g0 + slot];
             const int start = s.job_start[g0 + slot];
-            const int stop = s.job_stop[g0 + slot];
-            const int lim = (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1);
+            const int stop = OFS ? s.job_stop[g0 + slot] : p.nA;
+            const int lim = OFS ? (stop + kPerLoad<CB> - 1) & ~(kPerLoad<CB> - 1) : p.ldq;
             const int s_al = start & ~(kPerLoad<CB> - 1);
             int tgt = s.job_tgt[g0 + slot];
             const CB *row = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq;
@@ -569,7 +573,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 if (c0 >= __shfl_sync(0xFFFFFFFFu, *vbest, 0)) break;
                 my_bytes += sizeof(CB) * (unsigned long long)min(kChunk<CB>, lim - c0);
                 int t_used;
-                const int a = warp_scan_chunk<CB, F7>(row, ks, tk, R > Rps, c0, start, lim, stop, tgt,
+                const int a = warp_scan_chunk<CB, F7, OFS>(row, ks, tk, R > Rps, c0, start, lim, stop, tgt,
                                                       p.y_b + b, t_used, lane);
                 tgt = t_used;
                 if (a >= 0) {
@@ -588,11 +592,11 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
     __syncthreads();
     const unsigned long long tB = p.profile ? ptimer() : 0;
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
-        const int pair = s.job_pair[j];
+        const int pair = OFS ? s.job_pair[j] : -1;
         if (pair == -2) continue;  // a row's wrapped part: decided with the row's first job
         const int b = s.job_b[j];
         int a = s.job_best[j];
-        const int st = s.job_start[j], sp = s.job_stop[j];
+        const int st = s.job_start[j], sp = OFS ? s.job_stop[j] : p.nA;
         // entries examined: start .. a, or the whole range [start, stop)
         unsigned ex = a != 0x7FFFFFFF ? (unsigned)(a - st + 1) : (st < sp ? (unsigned)(sp - st) : 0u);
         int org = 0;  // PR_RULE_OFFSET: the row's first column in this phase
@@ -604,7 +608,7 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
                 ex += a2 != 0x7FFFFFFF ? (unsigned)(a2 + 1) : (unsigned)sp2;
             }
             org = sp2;
-        } else if (p.rule) {
+        } else if (OFS) {
             org = sp == p.nA ? 0 : sp;
         }
         cells += ex;
@@ -688,7 +692,7 @@ __host__ __device__ inline size_t slots_offset(int ldq, int key_bytes) {
 // shared memory) instead of a cooperative grid.  SL: a CTA whose jobs exceed
 // one register group scans them from per-warp shared-memory slots filled by
 // bulk copies (always with CL).
-template <class CB, bool CL, bool SL, bool F7>
+template <class CB, bool CL, bool SL, bool F7, bool OFS>
 __global__ void __launch_bounds__(kThreads, 1)
 k_phases(Params p, int warps_per_row, int rows_per_group) {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -820,7 +824,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
             const unsigned long long t_r1 = p.profile ? ptimer() : 0;
             unsigned long long t_mark = t_r1;
             // PR_RULE_OFFSET turns a row into up to two jobs: half as many per batch
-            const int per_batch = p.rule ? kBatch / 2 : kBatch;
+            const int per_batch = OFS ? kBatch / 2 : kBatch;
             for (int i0 = 0; i0 < nitems; i0 += per_batch) {
                 const int cnt = min(per_batch, nitems - i0);
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -845,7 +849,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                             start = -1 - y;
                             y = -1;
                         }
-                        if (p.rule) {  // once round the row from its seeded first column
+                        if (OFS) {  // once round the row from its seeded first column
                             start = phase_offset(phase + 1, b, p.nA);
                             wrap = start;
                         }
@@ -858,7 +862,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                         y = q.z;
                         // PR_RULE_OFFSET (first column q.w): before the wrap the rest
                         // of the row and then [0, q.w); after it, up to q.w
-                        if (q.w > 0) {
+                        if (OFS && q.w > 0) {
                             if (q.y >= q.w) wrap = q.w;
                             else stop = q.w;
                         }
@@ -868,10 +872,12 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     const int j = atomicAdd(&s.njob, nj);
                     s.job_b[j] = b;
                     s.job_start[j] = start;
-                    s.job_stop[j] = stop;
                     s.job_tgt[j] = tg;
-                    s.job_pair[j] = nj == 2 ? j + 1 : -1;
-                    if (nj == 2) {
+                    if (OFS) {
+                        s.job_stop[j] = stop;
+                        s.job_pair[j] = nj == 2 ? j + 1 : -1;
+                    }
+                    if (OFS && nj == 2) {
                         s.job_b[j + 1] = b;
                         s.job_start[j + 1] = 0;
                         s.job_stop[j + 1] = wrap;
@@ -881,7 +887,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 }
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += ptimer() - t_mark;
-                run_jobs<CB, SL, F7>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
+                run_jobs<CB, SL, F7, OFS>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
                                  &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate, cells);
                 if (p.profile) t_mark = ptimer();
             }
@@ -1147,30 +1153,35 @@ struct PhaseCfg {
     size_t smem = 0;
 };
 
-template <class CB, bool CL, bool SL, bool F7>
+template <class CB, bool CL, bool SL, bool F7, bool OFS = false>
 pr_status set_phase_attrs(size_t smem) {
-    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7, OFS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CL) PR_CUDA(cudaFuncSetAttribute(k_phases<CB, CL, SL, F7, OFS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return PR_OK;
 }
 
 // The phase kernel for the storage type (cb8: bytes), the form (cl: one
-// cluster, sl: row slots) and the byte pre-test (f7: floor(1/eps) <= 125).
-const void *phase_kernel(bool cb8, bool cl, bool sl, bool f7) {
+// cluster, sl: row slots), the byte pre-test (f7: floor(1/eps) <= 125) and
+// the step I rule (ofs: PR_RULE_OFFSET).
+template <bool OFS>
+const void *phase_kernel_of(bool cb8, bool cl, bool sl, bool f7) {
     if (!cb8)
-        return cl ? (const void *)k_phases<uint16_t, true, true, false>
-                  : sl ? (const void *)k_phases<uint16_t, false, true, false>
-                       : (const void *)k_phases<uint16_t, false, false, false>;
+        return cl ? (const void *)k_phases<uint16_t, true, true, false, OFS>
+                  : sl ? (const void *)k_phases<uint16_t, false, true, false, OFS>
+                       : (const void *)k_phases<uint16_t, false, false, false, OFS>;
     if (f7)
-        return cl ? (const void *)k_phases<uint8_t, true, true, true>
-                  : sl ? (const void *)k_phases<uint8_t, false, true, true>
-                       : (const void *)k_phases<uint8_t, false, false, true>;
-    return cl ? (const void *)k_phases<uint8_t, true, true, false>
-              : sl ? (const void *)k_phases<uint8_t, false, true, false>
-                   : (const void *)k_phases<uint8_t, false, false, false>;
+        return cl ? (const void *)k_phases<uint8_t, true, true, true, OFS>
+                  : sl ? (const void *)k_phases<uint8_t, false, true, true, OFS>
+                       : (const void *)k_phases<uint8_t, false, false, true, OFS>;
+    return cl ? (const void *)k_phases<uint8_t, true, true, false, OFS>
+              : sl ? (const void *)k_phases<uint8_t, false, true, false, OFS>
+                   : (const void *)k_phases<uint8_t, false, false, false, OFS>;
+}
+const void *phase_kernel(bool cb8, bool cl, bool sl, bool f7, bool ofs) {
+    return ofs ? phase_kernel_of<true>(cb8, cl, sl, f7) : phase_kernel_of<false>(cb8, cl, sl, f7);
 }
 
-// Largest cluster (16, else 8) of k_phases<CB, true, true, false> the device can hold, or 0.
+// Largest cluster (16, else 8) of k_phases<CB, true, true, false, false> the device can hold, or 0.
 template <class CB>
 int max_phase_cluster(size_t smem) {
     for (int cs : {16, 8}) {
@@ -1186,7 +1197,7 @@ int max_phase_cluster(size_t smem) {
         c.attrs = at;
         c.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true, true, false>, &c) == cudaSuccess && n >= 1)
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_phases<CB, true, true, false, false>, &c) == cudaSuccess && n >= 1)
             return cs;
         cudaGetLastError();  // clear a refusal of this size
     }
@@ -1215,10 +1226,19 @@ pr_status phase_cfg(PhaseCfg &cfg) {
     if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, false, true>(smem);
     if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true, true>(smem);
     if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, false, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, false, true, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint16_t, true, true, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, false, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true, false, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, false, true, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, false, true, true, true>(smem);
+    if (rc == PR_OK) rc = set_phase_attrs<uint8_t, true, true, true, true>(smem);
     if (rc != PR_OK) return rc;
     int per_sm = 0, per_sm16 = 0;
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false, false, false>, kThreads, smem));
-    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false, false, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phases<uint8_t, false, false, false, false>, kThreads, smem));
+    PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm16, k_phases<uint16_t, false, false, false, false>, kThreads, smem));
     if (per_sm16 < per_sm) per_sm = per_sm16;
     if (per_sm < 1) return fail(PR_ERR_INVALID, "phase kernel does not fit on an SM");
     int grid = di.sms * per_sm;
@@ -1357,12 +1377,12 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
         c.numAttrs = 1;
         Params pc = p;
         void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
-        PR_CUDA(cudaLaunchKernelExC(&c, phase_kernel(cb8, true, true, f7), args));
+        PR_CUDA(cudaLaunchKernelExC(&c, phase_kernel(cb8, true, true, f7, p.rule != 0), args));
     } else {
         Params pc = p;
         void *args[] = {(void *)&pc, (void *)&warps_per_row, (void *)&rows_per_group};
         const bool sl = use_slots_in_grid(p.nslots);
-        const void *fn = phase_kernel(cb8, false, sl, f7);
+        const void *fn = phase_kernel(cb8, false, sl, f7, p.rule != 0);
         const size_t smem = sl ? slots_offset(p.ldq, kb) + (size_t)p.nslots * p.slot_bytes : smem_bytes(p.ldq, kb);
         PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, smem, st));
     }
