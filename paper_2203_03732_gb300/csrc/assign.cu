@@ -1079,9 +1079,52 @@ k_finish(Params p, Src src, int *match_b, int *match_a, int *free_b, int *free_a
 // ---------------------------------------------------------------------------
 // Costs from points (points.cuh), over the same (row, group of 8 columns)
 // grid stride as k_quantise: first the largest distance, then Eq. (1) on
-// c = RN32(d / max d), exactly as for a stored FP32 cost.
+// c = RN32(d / max d), exactly as for a stored FP32 cost.  The largest
+// distance is taken over the squared sums: the IEEE square root is correctly
+// rounded and non-decreasing, so the root of the largest sum is the largest
+// root.
 // ---------------------------------------------------------------------------
-__global__ void k_points_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim, int squared,
+// The squared sums of row point xb against the 8 column points a0 .. a0+7
+// (entries past n_A are left alone).  D > 0: dim == D with XA 16-byte
+// aligned, so a group of 8 points is whole 16-byte loads (2 * D of them);
+// D == 0: any dim, one coordinate at a time.  Same IEEE operations in the
+// same order either way (dist_f32).
+template <int D>
+__device__ __forceinline__ void sq_group8(const float *__restrict__ XA, const float *__restrict__ xb, int dim,
+                                          int a0, int nA, float (&d)[8]) {
+    if (D > 0 && a0 + 8 <= nA) {
+        float x[8 * (D > 0 ? D : 1)];
+        const float4 *v = reinterpret_cast<const float4 *>(XA + (long long)a0 * D);
+#pragma unroll
+        for (int q = 0; q < 2 * D; ++q) {
+            const float4 t = __ldg(v + q);
+            x[4 * q] = t.x;
+            x[4 * q + 1] = t.y;
+            x[4 * q + 2] = t.z;
+            x[4 * q + 3] = t.w;
+        }
+        float xbk[D > 0 ? D : 1];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xbk[k] = xb[k];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = __fsub_rn(xbk[k], x[j * D + k]);
+                const float sq = __fmul_rn(t, t);
+                acc = k == 0 ? sq : __fadd_rn(acc, sq);
+            }
+            d[j] = acc;
+        }
+        return;
+    }
+    for (int j = 0; j < 8; ++j)
+        if (a0 + j < nA) d[j] = dist_f32(xb, XA + (long long)(a0 + j) * dim, dim, 1);
+}
+
+template <int D>
+__global__ void k_points_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
                              int nB, int nA, int ldq, unsigned *maxbits) {
     const long long groups = (long long)nB * (ldq >> 3);
     float m = 0.0f;
@@ -1089,34 +1132,35 @@ __global__ void k_points_max(const float *__restrict__ XA, const float *__restri
          g += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(g / (ldq >> 3));
         const int a0 = (int)(g - (long long)b * (ldq >> 3)) << 3;
-        const float *xb = XB + (long long)b * dim;
-        for (int j = 0; j < 8 && a0 + j < nA; ++j)
-            m = fmaxf(m, dist_f32(xb, XA + (long long)(a0 + j) * dim, dim, squared));
+        float d[8];
+        sq_group8<D>(XA, XB + (long long)b * dim, dim, a0, nA, d);
+        for (int j = 0; j < 8 && a0 + j < nA; ++j) m = fmaxf(m, d[j]);
     }
     // non-negative floats order like their bit patterns (NaN is dropped by fmaxf)
     const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(maxbits, mx);
 }
 
-template <class CB>
+template <class CB, int D>
 __global__ void k_points_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim, int squared,
                                int nB, int nA, int ldq, const unsigned *__restrict__ maxbits, EpsSplit e,
                                CB *__restrict__ cb, WsHead *head) {
     constexpr uint32_t kPad = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
     const long long groups = (long long)nB * (ldq >> 3);
-    const float M = __uint_as_float(*maxbits);
+    const float M = squared ? __uint_as_float(*maxbits) : __fsqrt_rn(__uint_as_float(*maxbits));
     bool bad = false;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
          g += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(g / (ldq >> 3));
         const int a0 = (int)(g - (long long)b * (ldq >> 3)) << 3;
-        const float *xb = XB + (long long)b * dim;
+        float sq[8];
+        sq_group8<D>(XA, XB + (long long)b * dim, dim, a0, nA, sq);
         uint32_t h[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int a = a0 + j;
             if (a < nA) {
-                const float d = dist_f32(xb, XA + (long long)a * dim, dim, squared);
+                const float d = squared ? sq[j] : __fsqrt_rn(sq[j]);
                 if (!(d >= 0.0f && d <= M)) {  // NaN or infinite coordinates
                     bad = true;
                     h[j] = 0;
@@ -1295,6 +1339,19 @@ struct CostSource {
     bool points = false;
 };
 
+// The two passes that form the rounded costs from points.
+template <int D>
+void launch_points(const CostSource &src, int n_rows, int n_cols, const Params &p, const EpsSplit &e, bool cb8,
+                   void *cbw, int qgrid, cudaStream_t st) {
+    k_points_max<D><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, n_rows, n_cols, p.ldq, &p.ctl->maxbits);
+    if (cb8)
+        k_points_quant<uint8_t, D><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
+                                                          p.ldq, &p.ctl->maxbits, e, (uint8_t *)cbw, &p.ctl->head);
+    else
+        k_points_quant<uint16_t, D><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
+                                                           p.ldq, &p.ctl->maxbits, e, (uint16_t *)cbw, &p.ctl->head);
+}
+
 // Everything after the argument checks, shared by pr_assign, pr_assign_points
 // and pr_assign_noalloc: p holds the workspace regions and sizes; this fills
 // the scalars, then enqueues init, rounding, the phase loop, decode and finish.
@@ -1326,15 +1383,12 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
     void *cbw = const_cast<void *>(p.cb);
     if (src.points) {
         const EpsSplit e = make_eps_split(eps);
-        k_points_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols, p.ldq,
-                                            &p.ctl->maxbits);
-        PR_CUDA(cudaGetLastError());
-        if (cb8)
-            k_points_quant<uint8_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
-                                                           p.ldq, &p.ctl->maxbits, e, (uint8_t *)cbw, &p.ctl->head);
-        else
-            k_points_quant<uint16_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
-                                                            p.ldq, &p.ctl->maxbits, e, (uint16_t *)cbw, &p.ctl->head);
+        // 2-D and 3-D points with 16-byte-aligned columns take whole-vector loads
+        const bool al = ((uintptr_t)src.XA % 16) == 0;
+        const int D = al && (src.dim == 2 || src.dim == 3) ? src.dim : 0;
+        if (D == 2) launch_points<2>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
+        else if (D == 3) launch_points<3>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
+        else launch_points<0>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
     } else if (dt == PR_F64 && cb8)
         launch_quantise<double, uint8_t>((const double *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint8_t *)cbw,
                                          &p.ctl->head, qgrid, st);
