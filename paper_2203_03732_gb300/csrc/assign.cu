@@ -53,9 +53,9 @@ namespace {
 
 constexpr int kThreads = 512;             // threads per CTA of the phase kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kUnroll = 8;                // 16-byte loads in flight per lane per chunk
+constexpr int kUnroll = 3;                // 16-byte loads in flight per lane per chunk (swept: 2..12 at n = 10,000; 3-4 best)
 // cbar elements per 16-byte load and per warp chunk (32 lanes x kUnroll
-// loads: 4 KiB) for the storage type CB
+// loads: 1.5 KiB) for the storage type CB
 template <class CB> constexpr int kPerLoad = 16 / (int)sizeof(CB);
 template <class CB> constexpr int kChunk = 32 * kPerLoad<CB> * kUnroll;
 // Byte form: used when floor(1/eps) <= 252.  cbar <= 252, every key

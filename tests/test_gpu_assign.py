@@ -2,7 +2,7 @@
 dual vectors and the phase/round counts; FP64 cost within 1e-12 relative).
 
 Sizes span one chunk, several chunks and ragged tails of the row scan
-(4096-column chunks, 8-column vectors), the unbalanced case, FP32 input,
+(1536-column byte chunks, 768-column 16-bit chunks, 8- and 16-column vectors), the unbalanced case, FP32 input,
 closed-form special cases, and the full n = 10,000 workloads.
 """
 import ctypes
