@@ -161,12 +161,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The sources the phase kernel is built from (its translation unit and the
+# headers it includes): the captured DRAM traffic stays valid while they do.
+PHASE_SOURCES = ("assign.cu", "scan_common.cuh", "quantise.cuh", "points.cuh", "prot_internal.cuh")
+
+
 def src_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2203_03732_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in PHASE_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "prot.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
