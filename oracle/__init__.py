@@ -35,6 +35,7 @@ MODE_REVERSE = 4
 MODE_SEQUENTIAL = 8
 MODE_EVICT_RESUME = 16
 MODE_OFFSET = 32
+MODE_PARALLEL = 64
 
 
 class Stats(ctypes.Structure):

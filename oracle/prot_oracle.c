@@ -250,7 +250,13 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
                 ++r;
                 /* Proposals of round r, all made against the taken[] state
                  * left by rounds 1..r-1. */
-                int32_t nprop = 0;
+                /* The scans of a round read only the taken[] state and duals
+                 * fixed for the round and write per-row state, so they may
+                 * run in any order or at once (OR_MODE_PARALLEL: OpenMP over
+                 * the active rows, for timing on all host cores); the
+                 * lowest proposer of each column is taken afterwards. */
+                int64_t scanned = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : scanned) if (mode & OR_MODE_PARALLEL)
                 for (int32_t i = 0; i < nact; ++i) {
                     int32_t b = act[i];
                     int32_t start = (mode & OR_MODE_LITERAL) ? 0 : ptr[b];
@@ -263,20 +269,25 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
                             int32_t a = ptr[b];
                             ptr[b] = (a + 1 == nA) ? 0 : a + 1;
                             covered[b] += 1;
-                            st->scanned += 1;
+                            scanned += 1;
                             if (taken[a] == 0 && admissible(cb, nA, y_b, y_a, b, a)) { p = a; break; }
                         }
                     } else
                     for (int32_t a = start; a < nA; ++a) {
-                        st->scanned += 1;
+                        scanned += 1;
                         if (taken[a] == 0 && admissible(cb, nA, y_b, y_a, b, a)) { p = a; break; }
                     }
                     prop[b] = p;
+                    if (p < 0) ptr[b] = nA;
+                }
+                st->scanned += scanned;
+                int32_t nprop = 0;
+                for (int32_t i = 0; i < nact; ++i) {
+                    int32_t b = act[i];
+                    int32_t p = prop[b];
                     if (p >= 0) {
                         ++nprop;
                         if (b < best[p]) best[p] = b;
-                    } else {
-                        ptr[b] = nA;
                     }
                 }
                 if (nprop == 0) break;

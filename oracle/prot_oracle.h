@@ -17,6 +17,8 @@
 #define OR_MODE_CHECK 2       /* check (I1)/(I2) after every phase          */
 #define OR_MODE_REVERSE 4     /* process B' in descending order             */
 #define OR_MODE_SEQUENTIAL 8  /* the paper's sequential greedy (Lemma 3.4)  */
+#define OR_MODE_PARALLEL 64 /* the scans of a round on all host cores (OpenMP);
+                               same results                                  */
 #define OR_MODE_OFFSET 32   /* step I rule with seeded start columns: in phase
                                p every free row b scans cyclically from
                                column splitmix64(p << 32 | b) mod |A|        */

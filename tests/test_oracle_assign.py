@@ -469,3 +469,16 @@ def test_offset_rule_breaks_the_round_convoy():
     off = oracle.assign_int(cb, T, mode=oracle.MODE_OFFSET)["stats"]
     assert low["phases"] == off["phases"] == 1
     assert off["rounds"] * 4 < low["rounds"]
+
+
+@pytest.mark.parametrize("mode", [0, 32])
+def test_parallel_scans_change_nothing(mode):
+    """OR_MODE_PARALLEL (the scans of a round on all host cores, for timing)
+    gives the same matching, duals and counters as the serial oracle."""
+    C = W.assignment_euclid_2d(700, 12)
+    for eps in (0.1, 0.01):
+        r0 = oracle.assign(C, eps, mode=mode)
+        r1 = oracle.assign(C, eps, mode=mode | oracle.MODE_PARALLEL)
+        for k in ("row_to_col", "col_to_row", "y_row", "y_col"):
+            assert np.array_equal(r0[k], r1[k])
+        assert r0["stats"] == r1["stats"] and r0["cost"] == r1["cost"]
