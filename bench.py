@@ -392,9 +392,37 @@ def run_extras(a, torch, prot, W, dev, stream):
 
     ex["ot"] = run_ot(a, torch, prot, W, dev, reps=3)
     ex["mnist_shaped"] = run_mnist_shaped(a, torch, prot, W, dev, stream)
+    ex["assign_n1000"] = run_n1000(a, torch, prot, W, dev, stream)
     if not a.no_cpu_baseline:
         ex["oracle_all_cores"] = time_oracle_parallel(a, W)
     return ex
+
+
+def run_n1000(a, torch, prot, W, dev, stream):
+    """The small configuration: n = 1000 uniform 2-D points per side, squared
+    Euclidean cost / max, eps = 0.1, 30 seeds; GPU solve time (median over
+    seeds of 10 timed solves each) and the single-thread oracle on the same
+    inputs."""
+    import statistics
+    import oracle
+    gpu, cpu, phases, rounds = [], [], [], []
+    ws = prot.Workspace(dev)
+    for seed in range(30):
+        Cn = W.assignment_sq_euclid_2d(1000, seed)
+        Ct = torch.from_numpy(Cn).to(dev)
+        r = prot.assign(Ct, 0.1, ws=ws)
+        out = {k: v for k, v in r.items() if k != "stats"}
+        gpu.append(timed(torch, stream, lambda: prot.assign(Ct, 0.1, ws=ws, sync=False, out=out), 10))
+        phases.append(r["stats"]["phases"])
+        rounds.append(r["stats"]["rounds"])
+        if seed < 5 and not a.no_cpu_baseline:
+            t0 = time.perf_counter()
+            oracle.assign(Cn, 0.1)
+            cpu.append(1000.0 * (time.perf_counter() - t0))
+    return {"workload": "n=1000, 2-D uniform, squared Euclidean / max, eps=0.1, seeds 0..29",
+            "gpu_ms_median": statistics.median(gpu), "phases_median": statistics.median(phases),
+            "rounds_median": statistics.median(rounds),
+            "oracle_ms_1thread_median_5_seeds": statistics.median(cpu) if cpu else None}
 
 
 def time_oracle_parallel(a, W):
