@@ -55,8 +55,7 @@ namespace prot {
 namespace {
 
 constexpr int kOtThreads = 256;
-constexpr int kOtUnroll = 8;
-constexpr int kOtChunk = 32 * 8 * kOtUnroll;
+constexpr int kOtUnroll = 4;  // 2 KiB warp chunks (swept 3, 4, 8 at 10k x 10k)
 constexpr int kFlagSearching = 1, kFlagInBp = 2;
 constexpr int kFixUnroll = 8;  // plan-column chunks of 32 counts read at a time
 
@@ -220,7 +219,9 @@ __device__ __forceinline__ unsigned long long ot_phase_start(const OParams &p) {
 // Warp per searching supply vertex: the lowest a >= ptr with
 // cbar + kmin_a == F_b - 1 and avail_a > 0.
 // Returns this thread's proposals (lane 0 of each warp counts its rows).
-template <class CB>
+// F7: floor(1/eps) <= 125, so every sum of a real column's cbar and key
+// stays below 256 and the byte pre-test is one plain add (may_match<true>).
+template <class CB, bool F7>
 __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, unsigned long long &bytes_out) {
     constexpr int W = 16 / (int)sizeof(CB);  // columns per 16-byte load
     constexpr unsigned kAll = W == 16 ? 0xFFFFu : 0xFFu;
@@ -252,7 +253,7 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
                 if (idx < p.ldq) {
                     const uint4 kv = *reinterpret_cast<const uint4 *>(key + idx);
                     m = W == 8 ? eq_mask(make_uint4(cv[u].x + kv.x, cv[u].y + kv.y, cv[u].z + kv.z, cv[u].w + kv.w), t2)
-                               : eq_mask8(cv[u], kv, t2);
+                               : eq_mask8<F7>(cv[u], kv, t2);
                 }
                 const int lo = start - idx;
                 if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
@@ -364,7 +365,7 @@ __device__ __forceinline__ void ot_phase_end(const OParams &p) {
 // reads nothing until the loop is over.  The stop rule is Sec. 3.3 on the
 // copy instance: T = floor(eps * S), S the total supply copies, the phase cap
 // S (2K + 3) / (T + 1) + 1 with K = floor(1/eps).
-template <class CB>
+template <class CB, bool F7>
 __global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps, long long spin_limit) {
     OCtl *c = p.ctl;
     // invalid masses or costs (recorded by the earlier kernels of the solve):
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps
         ++phases;
         for (;;) {
             ++R;
-            const unsigned long long np = cta_sum(ot_propose<CB>(p, R, bytes));
+            const unsigned long long np = cta_sum(ot_propose<CB, F7>(p, R, bytes));
             if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, np, sum)) return;
             if (sum == 0) break;
             ++rounds;
@@ -826,7 +827,9 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     {
         // the phase loop: one cooperative launch, as many CTAs as fit (at
         // most 1023, the barrier's arrival field)
-        const void *loop = cb8 ? (const void *)k_ot_loop<uint8_t> : (const void *)k_ot_loop<uint16_t>;
+        const bool f7 = floor(1.0 / eps) <= 125.0;
+        const void *loop = !cb8 ? (const void *)k_ot_loop<uint16_t, false>
+                                : f7 ? (const void *)k_ot_loop<uint8_t, true> : (const void *)k_ot_loop<uint8_t, false>;
         int per_sm = 0;
         PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop, kOtThreads, 0));
         if (per_sm < 1) return fail(PR_ERR_INVALID, "pr_ot: loop kernel does not fit on an SM");

@@ -51,8 +51,10 @@ def test_matrix_batch_matches_oracle(prot, threads):
         off += int(n)
 
 
-@pytest.mark.parametrize("eps", [0.1, 0.01, 0.005])
+@pytest.mark.parametrize("eps", [0.1, 0.01, 0.005, 0.003])
 def test_points_batch_matches_oracle(prot, eps):
+    """Byte storage with the plain-add pre-test (eps 0.1, 0.01), with the
+    carry-isolated one (0.005), and 16-bit storage (0.003)."""
     import torch
     sizes = W.batched_sizes(24, 64, 700, seed=5)
     XA, XB, off = W.batched_points_3d(sizes, seed=5)
