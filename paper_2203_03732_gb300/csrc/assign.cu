@@ -187,19 +187,10 @@ __global__ void k_init(Params p, int *match_b) {
 // phase nothing is taken; in later rounds a candidate column is skipped when
 // its word carries a tag of an earlier round of this phase.
 // ---------------------------------------------------------------------------
-// Sum of 8 cbar values (packed 16-bit lanes) and their keys, from one
-// 16-byte load of uint16 cbar, or from half of a 16-byte load of uint8 cbar
-// (bytes widened to 16-bit lanes: byte j of x goes to lane j).
+// Sum of 8 cbar values and their keys (packed 16-bit lanes), from one
+// 16-byte load of uint16 cbar.
 __device__ __forceinline__ uint4 add_keys(uint4 c, uint4 k) {
     return make_uint4(c.x + k.x, c.y + k.y, c.z + k.z, c.w + k.w);
-}
-__device__ __forceinline__ uint4 widen_lo(uint4 x) {
-    return make_uint4(__byte_perm(x.x, 0, 0x4140), __byte_perm(x.x, 0, 0x4342),
-                      __byte_perm(x.y, 0, 0x4140), __byte_perm(x.y, 0, 0x4342));
-}
-__device__ __forceinline__ uint4 widen_hi(uint4 x) {
-    return make_uint4(__byte_perm(x.z, 0, 0x4140), __byte_perm(x.z, 0, 0x4342),
-                      __byte_perm(x.w, 0, 0x4140), __byte_perm(x.w, 0, 0x4342));
 }
 
 // Lowest candidate column in [c0, c0 + kChunk<CB>) that is >= start and not

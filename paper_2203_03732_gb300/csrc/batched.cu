@@ -29,8 +29,6 @@
 namespace prot {
 namespace {
 
-constexpr int kUnroll = 8;
-constexpr int kChunk = 32 * 8 * kUnroll;  // cbar elements per warp chunk
 constexpr int kMaxN = 5000;               // largest problem whose state fits shared memory
 constexpr int kRowBits = 13;              // a free-list entry: row | resume column << 13
 constexpr int kRowMask = (1 << kRowBits) - 1;
