@@ -1504,8 +1504,9 @@ pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, d
     if (rc != PR_OK) return rc;
     const Layout L = make_layout(n_rows, n_cols, cfg.grid);
     if (smem_bytes(L.ldq) > cfg.smem)
+        // each column costs 2 bytes of key copy and 1/8 byte of taken set
         return fail(PR_ERR_INVALID, "%s: n_cols = %d exceeds the shared-memory key copy (max %d)", who,
-                    n_cols, (int)((cfg.smem - smem_bytes(0)) * 16 / 33) & ~31);
+                    n_cols, (int)((cfg.smem - smem_bytes(0)) * 8 / 17) & ~31);
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total)
         return fail(PR_ERR_WORKSPACE, "%s: workspace NULL, not 256-byte aligned or < %zu bytes", who,
                     L.total);

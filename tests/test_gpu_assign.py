@@ -330,3 +330,27 @@ def test_mnist_shaped_workload(prot, eps):
     assert_parity(got, ref)
     opt, _ = oracle.hungarian(C)
     assert opt - 1e-9 <= got["cost"] <= opt + 3 * eps * 500 + 1e-9
+
+
+def test_widest_problem_the_key_copy_holds(prot):
+    """n_cols at the limit the library reports (the shared-memory copy of the
+    column keys and the taken set): parity with the oracle there, and
+    PR_ERR_INVALID from the host checks just past it."""
+    import re
+    import torch
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load()
+    dummy = torch.zeros(64, dtype=torch.float64, device="cuda")
+    st = _lib.PrStats()
+    rc = L.pr_assign(dummy.data_ptr(), 1, 1 << 23, 4, 1 << 23, 0.1, dummy.data_ptr(), dummy.data_ptr(),
+                     dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), ctypes.byref(st), None, 0, None)
+    assert rc == _lib.PR_ERR_INVALID
+    nmax = int(re.search(rb"max (\d+)", L.pr_last_error()).group(1))
+    assert 50000 < nmax < (1 << 20)
+    C = W.assignment_euclid_2d(40, 17, n_a=nmax)
+    got = gpu_solve(prot, C, 0.1)
+    assert_parity(got, oracle.assign(C, 0.1))
+    C2 = torch.rand(2, nmax + 32, dtype=torch.float64, device="cuda")
+    with pytest.raises(prot.PrError) as e:
+        prot.assign(C2, 0.1)
+    assert e.value.status == _lib.PR_ERR_INVALID
