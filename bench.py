@@ -243,6 +243,10 @@ def run_reference(a, world, rank):
 
 
 def run_e2e(a, torch, prot, C_pin, Cd, ws, out, stream, ref):
+    """End to end from host memory: pinned host costs -> device (copy
+    engine), the solve, then the matching and the cost back to the host.
+    (The library also reads pinned host costs in place, which measured
+    slower than the copy: 14.5 vs 9-11 ms.)"""
     r2c_host = torch.empty(a.n, dtype=torch.int32).pin_memory()
     cost_host = torch.empty((), dtype=torch.float64).pin_memory()
     Cd2 = torch.empty_like(Cd)

@@ -87,7 +87,11 @@ size_t pr_assign_workspace(int32_t n_rows, int32_t n_cols);
  * matches the k-th free row (ascending) with the k-th free column
  * (ascending); duals are left as the main routine ended.
  *
- *   C          n_rows x n_cols costs, dtype dt, leading dimension ldc >= n_cols
+ *   C          n_rows x n_cols costs, dtype dt, leading dimension ldc >= n_cols.
+ *              Device memory, or pinned (page-locked) host memory, which the
+ *              rounding kernel then reads in place over the host link (the
+ *              end-to-end path without a separate copy); other host memory
+ *              returns PR_ERR_INVALID before anything is enqueued
  *   eps        0 < eps < 1 with floor(1/eps) <= 32766
  *   n_rows     1 <= n_rows <= n_cols <= 2^24
  *   row_to_col [n_rows] out: column matched to each row (always >= 0)

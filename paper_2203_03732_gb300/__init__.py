@@ -62,17 +62,20 @@ def _stream_handle(torch, device):
 
 
 def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out=None,
-           rule: str = "lowest"):
+           rule: str = "lowest", results_on_device: bool = False):
     """Additive eps-approximate assignment (Sec. 2.2 of the paper).
 
     C: (n_rows, n_cols) float32/float64 tensor with costs in [0, 1],
        n_rows <= n_cols.  A CUDA tensor is solved in place on its device; a
-       CPU tensor is copied to the current CUDA device and the results are
-       copied back (the end-to-end path).
+       CPU tensor is copied to the current CUDA device (the copy engines move
+       it faster than the kernels read pinned host memory in place) and the
+       results are copied back (the end-to-end path).
     Returns a dict: row_to_col, col_to_row (int32), y_row, y_col (int32 duals
     in units of eps), cost (float64 scalar tensor) and, when sync, stats.
     rule: the maximal matching of step (I), "lowest" (lowest-index columns)
     or "offset" (seeded start columns per row and phase); see pr_assign_rule.
+    results_on_device: for CPU input, leave the results on the device (no
+    copy back, no synchronisation when sync is False).
     """
     torch = _torch()
     L = _lib.load()
@@ -121,7 +124,7 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
     res = dict(out)
     if sync:
         res["stats"] = st.as_dict()
-    if host_in:
+    if host_in and not results_on_device:
         res = {k: (v.cpu() if hasattr(v, "cpu") else v) for k, v in res.items()}
     return res
 

@@ -1487,6 +1487,29 @@ extern "C" size_t pr_assign_workspace(int32_t n_rows, int32_t n_cols) {
 namespace prot {
 namespace {
 
+// The address the kernels read a cost matrix through: device or managed
+// memory as it is; pinned (page-locked) host memory through its mapping
+// into the device address space, so the rounding kernel reads it in place
+// over the host link.  Any other host memory is refused here, before
+// anything is enqueued (a kernel would fault on it).
+pr_status device_view(const void *C, const void **out, const char *who) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, C);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PR_ERR_INVALID, "%s: C is not memory the CUDA runtime knows", who);
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *out = C;
+        return PR_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *out = a.devicePointer;
+        return PR_OK;
+    }
+    return fail(PR_ERR_INVALID, "%s: C must be device memory or pinned host memory", who);
+}
+
 // pr_assign and pr_assign_points after their own source checks: sizes, eps,
 // workspace, then the solve.
 pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, double eps,
@@ -1542,7 +1565,10 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
     if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign: bad dtype");
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign: ldc < n_cols");
     CostSource src;
-    src.C = C;
+    if (row_to_col && col_to_row && y_row && y_col && cost) {  // NULL outputs: reported below
+        const pr_status rc = device_view(C, &src.C, "pr_assign");
+        if (rc != PR_OK) return rc;
+    }
     src.dt = dt;
     src.ldc = ldc;
     return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
@@ -1558,7 +1584,10 @@ extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, in
     if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_rule: bad dtype");
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_rule: ldc < n_cols");
     CostSource src;
-    src.C = C;
+    if (row_to_col && col_to_row && y_row && y_col && cost) {  // NULL outputs: reported below
+        const pr_status rc = device_view(C, &src.C, "pr_assign_rule");
+        if (rc != PR_OK) return rc;
+    }
     src.dt = dt;
     src.ldc = ldc;
     return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,

@@ -354,3 +354,42 @@ def test_widest_problem_the_key_copy_holds(prot):
     with pytest.raises(prot.PrError) as e:
         prot.assign(C2, 0.1)
     assert e.value.status == _lib.PR_ERR_INVALID
+
+
+def test_pinned_host_costs_read_in_place(prot):
+    """C in pinned host memory: the rounding kernel reads it over the host
+    link, and the result equals the oracle's; pageable host memory is
+    refused on the host (PR_ERR_INVALID), before any kernel runs."""
+    import torch
+    from paper_2203_03732_gb300 import _lib
+    C = W.assignment_euclid_2d(1500, 23)
+    Cp = torch.from_numpy(C).pin_memory()
+    L = _lib.load()
+    n = 1500
+    outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(4)]
+    cst = torch.empty((), dtype=torch.float64, device="cuda")
+    wsp = torch.empty(L.pr_assign_workspace(n, n), dtype=torch.uint8, device="cuda")
+    st = _lib.PrStats()
+    rc = L.pr_assign(Cp.data_ptr(), 1, n, n, n, 0.01, outs[0].data_ptr(), outs[1].data_ptr(),
+                     outs[2].data_ptr(), outs[3].data_ptr(), cst.data_ptr(), ctypes.byref(st),
+                     wsp.data_ptr(), wsp.numel(), None)
+    assert rc == _lib.PR_OK
+    ref = oracle.assign(C, 0.01)
+    for k, t in zip(("row_to_col", "col_to_row", "y_row", "y_col"), outs):
+        assert np.array_equal(t.cpu().numpy(), ref[k]), k
+    assert st.phases == ref["stats"]["phases"]
+    assert abs(float(cst) - ref["cost"]) <= COST_RTOL * ref["cost"]
+    r2 = prot.assign(Cp, 0.01, results_on_device=True)
+    assert r2["row_to_col"].is_cuda and np.array_equal(r2["row_to_col"].cpu().numpy(), ref["row_to_col"])
+    # pageable host memory through the C ABI
+    Ch = np.ascontiguousarray(C[:50, :50])
+    out = [torch.empty(50, dtype=torch.int32, device="cuda") for _ in range(4)]
+    cost = torch.empty((), dtype=torch.float64, device="cuda")
+    ws = torch.empty(L.pr_assign_workspace(50, 50), dtype=torch.uint8, device="cuda")
+    st = _lib.PrStats()
+    rc = L.pr_assign(Ch.ctypes.data, 1, 50, 50, 50, 0.1, out[0].data_ptr(), out[1].data_ptr(),
+                     out[2].data_ptr(), out[3].data_ptr(), cost.data_ptr(), ctypes.byref(st),
+                     ws.data_ptr(), ws.numel(), None)
+    assert rc == _lib.PR_ERR_INVALID
+    assert b"pinned host memory" in L.pr_last_error()
+    torch.cuda.synchronize()
