@@ -266,11 +266,17 @@ size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem);
  * The matched copies give mass(b,a) = copies / theta; a demand that received
  * more than its mass gives the excess back from its highest-index supplier,
  * and every supply's remainder is routed north-west-corner style (supplies
- * ascending, demands ascending) into the remaining demand capacity.
+ * ascending, demands ascending) into the remaining demand capacity.  The
+ * paper leaves this fix-up to another paper; here the remainders are first
+ * rounded down to whole units of 2^-62 and the rule runs on exact integers
+ * (each supply loses less than 2^-62 of its mass).
  *
  *   C           n_sup x n_dem costs in [0,1] (rows = supplies B), ldc >= n_dem
  *   supply      [n_sup] FP64 masses nu >= 0 summing to 1 (device)
- *   demand      [n_dem] FP64 masses mu >= 0 summing to 1 (device)
+ *   demand      [n_dem] FP64 masses mu >= 0 summing to 1 (device); the
+ *               demand must cover the supply (else PR_ERR_NO_CONVERGENCE).
+ *               PR_ERR_INVALID for a negative or NaN mass, a mass >= 2, or
+ *               a side whose floor(m 2^32) sum to 1.5 * 2^32 or more
  *   plan_row, plan_col, plan_mass  [plan_cap] out: the plan as (supply,
  *               demand, mass) triples, each pair at most once
  *   plan_nnz    [1] out: number of triples (also written when > plan_cap,
@@ -281,8 +287,8 @@ size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem);
  *               -dem_kmin (dem_lo copies) and -dem_kmin - 1 (dem_hi copies)
  *   cost        [1] out: sum of mass * C over the plan (FP64)
  *   stats       host, may be NULL
- * The phase loop is driven from the host (one counter read per round), so
- * pr_ot synchronises `stream`.
+ * pr_ot synchronises `stream`: the host reads the phase loop's outcome and
+ * the plan size before the plan is written.
  */
 pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_sup, int32_t n_dem,
                 const double *supply, const double *demand, double eps, int64_t plan_cap,

@@ -65,6 +65,18 @@ def ot_phase_cap(eps, S_total):
     return (S_total * (2 * K + 3)) // (T + 1) + 1
 
 
+def fixup(C, nu, mu, theta_, cnt):
+    """The plan from matched copy counts cnt [nB][nA] and the fix-up alone:
+    returns (dense FP64 mass, FP64 cost)."""
+    C = np.ascontiguousarray(C, np.float64)
+    nB, nA = C.shape
+    mass = np.empty((nB, nA), np.float64)
+    cost = float(lib().or_ot_fixup(C, nA, nB, nA, np.ascontiguousarray(nu, np.float64),
+                                   np.ascontiguousarray(mu, np.float64), float(theta_),
+                                   np.ascontiguousarray(cnt, np.int32), mass))
+    return mass, cost
+
+
 def ot(C, nu, mu, eps, mode=0):
     """Whole OT oracle: Sec. 4 scaling, cluster phases, plan, fix-up, cost."""
     C = np.ascontiguousarray(C, np.float64)

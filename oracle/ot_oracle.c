@@ -46,8 +46,9 @@
  * Demand a that received more than mu_a gives the excess back from its
  * highest-index suppliers first; then every supply's unsent remainder is
  * routed north-west-corner style (b ascending, a ascending) into the
- * remaining demand capacity.  cost = sum mass * c, FP64, Neumaier-compensated
- * in (b, a) ascending order.
+ * remaining demand capacity, on the remainders rounded down to whole units
+ * of 2^-62 so that the rule runs in exact integer arithmetic.  cost = sum
+ * mass * c, FP64, Neumaier-compensated in (b, a) ascending order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -212,6 +213,21 @@ int or_ot_counts(const double *nu, const double *mu, int32_t nB, int32_t nA, dou
         if (!(mu[a] >= 0.0) || v > 2147483647.0) return OR_ERR_INVALID;
         D[a] = (int32_t)v;
     }
+    /* The masses of each side must sum to 1.  Refused: a mass of 2 or more,
+     * or a side whose floor(m * 2^32) add up to 1.5 * 2^32 or more (an exact
+     * integer sum, so the decision does not depend on the summation order).
+     * What passes sums to below 2, which keeps the fix-up's 2^-62 units of
+     * every residual and of their totals below 2^63. */
+    for (int side = 0; side < 2; ++side) {
+        const double *m = side ? mu : nu;
+        const int32_t n = side ? nA : nB;
+        uint64_t units = 0;
+        for (int32_t k = 0; k < n; ++k) {
+            if (!(m[k] < 2.0)) return OR_ERR_INVALID;
+            units += (uint64_t)(m[k] * 0x1p32);
+        }
+        if (units >= 3ull << 31) return OR_ERR_INVALID;
+    }
     return OR_OK;
 }
 
@@ -256,16 +272,26 @@ double or_ot_fixup(const double *C, int64_t ldc, int32_t nB, int32_t nA, const d
         rres[b] = nu[b] - sent;
         if (rres[b] < 0.0) rres[b] = 0.0;
     }
-    /* north-west corner over the residuals */
+    /* North-west corner over the residuals, in exact integer units of 2^-62:
+     * each residual is first rounded down to a whole number of units (the
+     * product by 2^62 is exact; it loses less than 2^-62 per vertex), the
+     * rule then runs on integers, and each allocation becomes t * 2^-62 in
+     * FP64 (one rounding, to nearest). */
+    uint64_t *ru = (uint64_t *)malloc(sizeof(uint64_t) * nB);
+    uint64_t *qu = (uint64_t *)malloc(sizeof(uint64_t) * nA);
+    for (int32_t b = 0; b < nB; ++b) ru[b] = rres[b] > 0.0 ? (uint64_t)(rres[b] * 0x1p62) : 0;
+    for (int32_t a = 0; a < nA; ++a) qu[a] = q[a] > 0.0 ? (uint64_t)(q[a] * 0x1p62) : 0;
     int32_t i = 0, j = 0;
     while (i < nB && j < nA) {
-        if (rres[i] <= 0.0) { ++i; continue; }
-        if (q[j] <= 0.0) { ++j; continue; }
-        double t = rres[i] < q[j] ? rres[i] : q[j];
-        mass[(int64_t)i * nA + j] += t;
-        rres[i] -= t;
-        q[j] -= t;
+        if (ru[i] == 0) { ++i; continue; }
+        if (qu[j] == 0) { ++j; continue; }
+        uint64_t t = ru[i] < qu[j] ? ru[i] : qu[j];
+        mass[(int64_t)i * nA + j] += (double)t * 0x1p-62;
+        ru[i] -= t;
+        qu[j] -= t;
     }
+    free(ru);
+    free(qu);
     double s = 0.0, comp = 0.0;
     for (int32_t b = 0; b < nB; ++b)
         for (int32_t a = 0; a < nA; ++a) {

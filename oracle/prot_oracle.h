@@ -64,8 +64,13 @@ int or_ot_cluster_int(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *
 int64_t or_ot_check(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *F, const int32_t *f,
                     const int32_t *kmin, const int32_t *clo, const int32_t *chi, const void *unused);
 double or_ot_theta(int32_t nB, int32_t nA, double eps);
+/* S_b = floor(theta nu_b), D_a = ceil(theta mu_a); OR_ERR_INVALID for a
+ * negative or NaN mass, a mass >= 2, or a side whose floor(m 2^32) sum to
+ * 1.5 * 2^32 or more (the masses must sum to 1). */
 int or_ot_counts(const double *nu, const double *mu, int32_t nB, int32_t nA, double eps,
                  int32_t *S, int32_t *D);
+/* mass = plan_cnt / theta, the demand trim, then the north-west corner over
+ * the residuals in whole units of 2^-62; returns the FP64 cost. */
 double or_ot_fixup(const double *C, int64_t ldc, int32_t nB, int32_t nA, const double *nu,
                    const double *mu, double theta, const int32_t *plan_cnt, double *mass);
 

@@ -37,8 +37,12 @@
 // gives the excess back from its highest supply index; each supply's unsent
 // remainder is routed north-west-corner style (b ascending, a ascending) into
 // the remaining demand capacity.  The FP64 arithmetic of the fix-up follows
-// one fixed order (ascending b per demand, ascending a per supply, then the
-// north-west walk), so the masses are reproducible bit for bit.
+// one fixed order (ascending b per demand, ascending a per supply), so the
+// residuals are reproducible bit for bit.  The north-west rule then runs on
+// the residuals rounded down to whole units of 2^-62, in exact integers: an
+// allocation starts wherever a supply's or a demand's run of units starts in
+// the two prefix sums, so every allocation is found in parallel (a merge of
+// the two sorted lists of run starts) with the serial walk's result.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -68,12 +72,13 @@ struct OCtl {
     int n_extra;                // allocations on pairs without matched copies
     int pad;
     long long bytes;
+    unsigned long long mass_units[2];  // sum of floor(m 2^32) over supplies, demands
 };
 
 struct OLayout {
     size_t ctl, cb, key, S, D, F, f, r, ptr, pa, flag, kmin, clo, chi, avail, sel, granted, prop;
     size_t plane, nnz_a, off_a, trim_b, trim_t, q, rres, cnt_b, off_b, bsort_a, bsort_m, nw_flag,
-        nw_off, nw_b, nw_a, nw_t, total;
+        nw_off, nw_b, nw_a, nw_t, nw_pr, nw_pq, nw_pos, total;
     int ldq;
     size_t plane_elems;
 };
@@ -117,6 +122,9 @@ OLayout make_olayout(int nB, int nA) {
     L.nw_b = c.take<int>((size_t)nB + nA);
     L.nw_a = c.take<int>((size_t)nB + nA);
     L.nw_t = c.take<double>((size_t)nB + nA);
+    L.nw_pr = c.take<unsigned long long>(nB);
+    L.nw_pq = c.take<unsigned long long>(nA);
+    L.nw_pos = c.take<int>((size_t)nB + nA);
     L.total = c.total();
     return L;
 }
@@ -140,20 +148,40 @@ __device__ __forceinline__ int *hi_plane(const OParams &p, int a) {
     return p.plane + (size_t)(p.sel[a] ^ 1) * p.plane_elems + (size_t)a * p.nB;
 }
 
-// S_b = floor(theta nu_b), D_a = ceil(theta mu_a) (Sec. 4), one FP64 product each.
+// S_b = floor(theta nu_b), D_a = ceil(theta mu_a) (Sec. 4), one FP64 product
+// each.  Also sums floor(m 2^32) per side, exactly (each term < 2^33): the
+// host refuses a side whose sum reaches 1.5 * 2^32, and a mass of 2 or more
+// is refused here, so the fix-up's 2^-62 units and their totals stay below
+// 2^63.
 __global__ void k_ot_counts(const double *nu, const double *mu, int nB, int nA, double theta,
-                            int *S, int *D, WsHead *head) {
+                            int *S, int *D, OCtl *ctl) {
     const int stride = gridDim.x * blockDim.x;
+    unsigned long long us = 0, ud = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nB + nA; i += stride) {
         const bool sup = i < nB;
         const double m = sup ? nu[i] : mu[i - nB];
         const double v = sup ? floor(__dmul_rn(theta, m)) : ceil(__dmul_rn(theta, m));
-        if (!(m >= 0.0) || !(v <= 2147483647.0)) {
-            record_error(head, PR_ERR_INVALID);
+        if (!(m >= 0.0) || !(m < 2.0) || !(v <= 2147483647.0)) {
+            record_error(&ctl->head, PR_ERR_INVALID);
             continue;
         }
-        if (sup) S[i] = (int)v;
-        else D[i - nB] = (int)v;
+        const unsigned long long u = __double2ull_rz(__dmul_rn(m, 0x1p32));
+        if (sup) {
+            S[i] = (int)v;
+            us += u;
+        } else {
+            D[i - nB] = (int)v;
+            ud += u;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        us += __shfl_down_sync(0xFFFFFFFFu, us, o);
+        ud += __shfl_down_sync(0xFFFFFFFFu, ud, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (us) atomicAdd(&ctl->mass_units[0], us);
+        if (ud) atomicAdd(&ctl->mass_units[1], ud);
     }
 }
 
@@ -432,6 +460,7 @@ struct FixParams {
     int *cnt_b, *off_b, *bsort_a;
     int *nw_b, *nw_a;
     double *nw_t;
+    unsigned long long *nw_pr, *nw_pq;  // inclusive prefix sums of the residual units
     int *plan_row, *plan_col;
     double *plan_mass;
     long long plan_cap;
@@ -602,52 +631,133 @@ __global__ void k_fix_supply(FixParams fp) {
     }
 }
 
-// One thread: the north-west corner over the residuals (b ascending, a
-// ascending); residuals staged in shared memory when they fit.
-__global__ void k_fix_nw(FixParams fp, int use_smem, OCtl *ctl) {
-    extern __shared__ double sm[];
-    const OParams &p = fp.o;
-    double *rr = use_smem ? sm : fp.rres;
-    double *qq = use_smem ? sm + p.nB : fp.q;
-    if (use_smem) {
-        for (int i = threadIdx.x; i < p.nB; i += blockDim.x) rr[i] = fp.rres[i];
-        for (int i = threadIdx.x; i < p.nA; i += blockDim.x) qq[i] = fp.q[i];
+// A residual in whole units of 2^-62, rounded down (the product is exact;
+// residuals are below 2, so the units are below 2^63).
+__device__ __forceinline__ unsigned long long nw_units(double r) {
+    return r > 0.0 ? __double2ull_rz(__dmul_rn(r, 0x1p62)) : 0ull;
+}
+
+// How many of P[0..n) (non-decreasing) are <= v, and are < v.
+__device__ __forceinline__ int nw_count_le(const unsigned long long *P, int n, unsigned long long v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int nw_count_lt(const unsigned long long *P, int n, unsigned long long v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Two CTAs: inclusive prefix sums of the residual units, supplies (CTA 0)
+// and demands (CTA 1).  Each thread sums one contiguous run, one scan over
+// the threads gives its offset, then the run is written.
+__global__ void __launch_bounds__(1024) k_nw_prefix(FixParams fp) {
+    __shared__ unsigned long long warp_off[32];
+    const bool dem = blockIdx.x == 1;
+    const double *x = dem ? fp.q : fp.rres;
+    const int n = dem ? fp.o.nA : fp.o.nB;
+    unsigned long long *P = dem ? fp.nw_pq : fp.nw_pr;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    unsigned long long own = 0;
+    for (int k = lo; k < hi; ++k) own += nw_units(x[k]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_off[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = lane < nw ? warp_off[lane] : 0;
+        unsigned long long z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < nw) warp_off[lane] = z - w;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    // The walk is one chain of FP64 subtractions, so it runs in one thread.
-    // The two current residuals live in registers; the next entry is read only
-    // when one is used up.  Each step's t is the smaller residual, which
-    // therefore becomes exactly 0, so only the other one is subtracted.  The
-    // residuals are never negative, so every comparison is made on the bit
-    // patterns as integers (same order as the doubles; <= 0 also covers -0.0
-    // and any negative value), leaving one FP64 operation per step.
-    int i = 0, j = 0, n = 0;
-    long long r = p.nB > 0 ? __double_as_longlong(rr[0]) : 0, q = p.nA > 0 ? __double_as_longlong(qq[0]) : 0;
-    while (i < p.nB && j < p.nA) {
-        if (r <= 0) {
-            if (++i < p.nB) r = __double_as_longlong(rr[i]);
-            continue;
-        }
-        if (q <= 0) {
-            if (++j < p.nA) q = __double_as_longlong(qq[j]);
-            continue;
-        }
-        const bool rs = r < q;  // the supply residual is the smaller
-        const long long t = rs ? r : q;
-        fp.nw_b[n] = i;
-        fp.nw_a[n] = j;
-        fp.nw_t[n] = __longlong_as_double(t);
-        ++n;
-        if (rs) {
-            q = __double_as_longlong(__dsub_rn(__longlong_as_double(q), __longlong_as_double(t)));
-            r = 0;
-        } else {
-            r = __double_as_longlong(__dsub_rn(__longlong_as_double(r), __longlong_as_double(t)));
-            q = 0;
-        }
+    unsigned long long run = warp_off[warp] + inc - own;
+    for (int k = lo; k < hi; ++k) {
+        run += nw_units(x[k]);
+        P[k] = run;
     }
-    ctl->n_nw = n;
+}
+
+// Thread per supply and per demand: the start s of its run of units (the
+// exclusive prefix sum) and its place in the merged order of all starts
+// (supplies before demands on equal starts).  An allocation starts at s if
+// the run is not empty and s is below cap = min(totals), except a demand
+// whose run starts where a non-empty supply run starts: that allocation is
+// the supply's.  flag[place] marks the allocation; the merged order is the
+// serial walk's order.
+__global__ void k_nw_flags(FixParams fp, int *flag, int *place) {
+    const int nB = fp.o.nB, nA = fp.o.nA;
+    const unsigned long long *Pr = fp.nw_pr, *Pq = fp.nw_pq;
+    const unsigned long long cap = Pr[nB - 1] < Pq[nA - 1] ? Pr[nB - 1] : Pq[nA - 1];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nB + nA; k += gridDim.x * blockDim.x) {
+        int m, f = 0;
+        if (k < nB) {
+            const unsigned long long s = k ? Pr[k - 1] : 0ull;
+            // demands starting below s: demand 0 (start 0) and every j >= 1 with Pq[j-1] < s
+            m = k + (s > 0 ? 1 + nw_count_lt(Pq, nA - 1, s) : 0);
+            f = Pr[k] > s && s < cap;
+        } else {
+            const int j = k - nB;
+            const unsigned long long s = j ? Pq[j - 1] : 0ull;
+            // supplies starting at or below s: supply 0 and every i >= 1 with Pr[i-1] <= s
+            m = j + 1 + nw_count_le(Pr, nB - 1, s);
+            if (Pq[j] > s && s < cap) {
+                const int i = nw_count_le(Pr, nB, s);  // Pr[i] > s, as s < Pr[nB - 1]
+                f = (i ? Pr[i - 1] : 0ull) != s;
+            }
+        }
+        flag[m] = f;
+        place[k] = m;
+    }
+}
+
+// Thread per flagged start: the allocation (b, a, amount) that begins there,
+// written at its rank among the flagged starts.  A supply start s lies in
+// the demand run j with Pq[j-1] <= s < Pq[j], a demand start in the supply
+// run i likewise; the allocation ends at min(Pr[i], Pq[j]).
+__global__ void k_nw_write(FixParams fp, const int *flag, const int *place, const int *off, OCtl *ctl) {
+    const int nB = fp.o.nB, nA = fp.o.nA;
+    const unsigned long long *Pr = fp.nw_pr, *Pq = fp.nw_pq;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nB + nA; k += gridDim.x * blockDim.x) {
+        const int m = place[k];
+        if (!flag[m]) continue;
+        int i, j;
+        unsigned long long s;
+        if (k < nB) {
+            i = k;
+            s = i ? Pr[i - 1] : 0ull;
+            j = nw_count_le(Pq, nA, s);
+        } else {
+            j = k - nB;
+            s = j ? Pq[j - 1] : 0ull;
+            i = nw_count_le(Pr, nB, s);
+        }
+        const unsigned long long e = Pr[i] < Pq[j] ? Pr[i] : Pq[j];
+        const int o = off[m];
+        fp.nw_b[o] = i;
+        fp.nw_a[o] = j;
+        fp.nw_t[o] = __dmul_rn(__ull2double_rn(e - s), 0x1p-62);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_nw = off[nB + nA];
 }
 
 // Thread per north-west allocation: add it to the matched entry of (b, a)
@@ -796,7 +906,7 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     const int g1 = di.sms * 4;
     k_ot_ctl_init<<<1, 1, 0, st>>>(p.ctl);
     PR_CUDA(cudaGetLastError());
-    k_ot_counts<<<g1, 256, 0, st>>>(supply, demand, nB, nA, theta, p.S, p.D, &p.ctl->head);
+    k_ot_counts<<<g1, 256, 0, st>>>(supply, demand, nB, nA, theta, p.S, p.D, p.ctl);
     PR_CUDA(cudaGetLastError());
     // bytes for the rounded costs and keys when every cbar and key fits one
     // (floor(1/eps) <= 252, as in pr_assign)
@@ -842,6 +952,9 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
     PR_CUDA(cudaStreamSynchronize(st));
     if (h.head.err == PR_ERR_INVALID) return fail(PR_ERR_INVALID, "pr_ot: invalid costs or masses");
+    if (h.mass_units[0] >= (3ull << 31) || h.mass_units[1] >= (3ull << 31))
+        return fail(PR_ERR_INVALID, "pr_ot: the supply and the demand masses must each sum to 1 "
+                                    "(a side summing to more than 1.5 is refused)");
     if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
     const long long phases = h.phases, rounds = h.rounds, free_at_stop = h.free_at_stop, T = h.threshold;
     pr_status rc = PR_OK;
@@ -865,6 +978,8 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     fp.nw_b = (int *)(w + L.nw_b);
     fp.nw_a = (int *)(w + L.nw_a);
     fp.nw_t = (double *)(w + L.nw_t);
+    fp.nw_pr = (unsigned long long *)(w + L.nw_pr);
+    fp.nw_pq = (unsigned long long *)(w + L.nw_pq);
     fp.plan_row = plan_row;
     fp.plan_col = plan_col;
     fp.plan_mass = plan_mass;
@@ -891,11 +1006,13 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     k_fix_supply<<<(nB + 255) / 256, 256, 0, st>>>(fp);
     PR_CUDA(cudaGetLastError());
     {
-        const size_t need = (size_t)(nB + nA) * sizeof(double);
-        const int use_smem = need <= (size_t)di.max_smem_optin ? 1 : 0;
-        if (use_smem)
-            PR_CUDA(cudaFuncSetAttribute(k_fix_nw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-        k_fix_nw<<<1, 256, use_smem ? need : 0, st>>>(fp, use_smem, p.ctl);
+        // the north-west allocations; their flags and ranks use the arrays
+        // that the merge below then reuses
+        int *flag = (int *)(w + L.nw_flag), *off = (int *)(w + L.nw_off), *place = (int *)(w + L.nw_pos);
+        k_nw_prefix<<<2, 1024, 0, st>>>(fp);
+        k_nw_flags<<<g1, 256, 0, st>>>(fp, flag, place);
+        k_prefix<<<1, 1024, 0, st>>>(flag, nB + nA, off);
+        k_nw_write<<<g1, 256, 0, st>>>(fp, flag, place, off, p.ctl);
         PR_CUDA(cudaGetLastError());
     }
     {

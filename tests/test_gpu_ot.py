@@ -87,6 +87,40 @@ def test_ot_bad_masses(prot):
         prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.1)
 
 
+def test_ot_refuses_mass_sums(prot):
+    """A side whose masses sum to more than 1.5 (exactly: whose floor(m 2^32)
+    sum to 1.5 * 2^32 or more), or a mass of 2 or more, is refused with
+    PR_ERR_INVALID (what passes keeps the fix-up's 2^-62 units below 2^63);
+    the oracle refuses the same inputs."""
+    import torch
+    C, nu, mu = W.ot_euclid_2d(10, 12, 1)
+    for bad_nu, bad_mu in ((nu * 1.6, mu), (nu, mu * 1.6), (np.r_[2.0, nu[1:]], mu)):
+        with pytest.raises(prot.PrError) as e:
+            prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(bad_nu).cuda(),
+                    torch.from_numpy(bad_mu).cuda(), 0.1)
+        assert e.value.status == -1
+        with pytest.raises(ValueError):
+            O.counts(bad_nu, bad_mu, 0.1)
+    # below 1.5 is accepted (more demand than supply: every supply copy can match)
+    r, dense = gpu_ot(prot, C, nu, mu * 1.4, 0.1)
+    assert_ot_parity(r, dense, O.ot(C, nu, mu * 1.4, 0.1))
+
+
+@pytest.mark.parametrize("nB,nA,eps", [(64, 128, 0.25), (128, 64, 0.1), (128, 256, 0.3)])
+def test_ot_uniform_masses(prot, nB, nA, eps):
+    """Uniform masses 1/n: the residuals are whole multiples of one small
+    unit, so supply and demand runs start at the same place in the
+    north-west walk (3, 8 and 5 times in these cases: the demand start is
+    then dropped), and many residuals are empty."""
+    C = W.assignment_euclid_2d(nB, 17, n_a=nA)
+    nu, mu = np.full(nB, 1.0 / nB), np.full(nA, 1.0 / nA)
+    r, dense = gpu_ot(prot, C, nu, mu, eps)
+    ref = O.ot(C, nu, mu, eps)
+    assert_ot_parity(r, dense, ref)
+    assert np.abs(dense.sum(1) - nu).max() <= 1e-12
+    assert (dense.sum(0) - mu).max() <= 1e-12
+
+
 def test_ot_barrier_timeout_reported_not_hung(prot, monkeypatch):
     """The loop kernel's grid barriers wait at most PR_SPIN_LIMIT_CYCLES: with
     one cycle every CTA gives up at its first barrier, pr_ot returns

@@ -125,3 +125,76 @@ def test_zero_masses_and_concentrated_supply():
     assert np.abs(r["mass"].sum(1) - nu).max() <= 1e-12
     assert (r["mass"][:, [0, 4]] == 0).all()
     assert r["cost"] <= lp_opt(C, nu, mu) + 3.5 * 0.1
+
+
+def test_north_west_by_hand():
+    """The fix-up alone (no matched copies): the north-west corner rule on
+    dyadic masses, tables worked by hand.  Every amount is a whole number of
+    2^-62 units below 2^53 of them, so each is exact in FP64."""
+    C = np.array([[0.5, 0.25, 1.0], [0.125, 0.75, 0.5], [1.0, 0.0, 0.25]])
+    z = np.zeros((3, 3), np.int32)
+    m, c = O.fixup(C, [0.5, 0.25, 0.25], [0.25, 0.5, 0.25], 10.0, z)
+    assert np.array_equal(m, [[0.25, 0.25, 0], [0, 0.25, 0], [0, 0, 0.25]])
+    assert c == 0.25 * 0.5 + 0.25 * 0.25 + 0.25 * 0.75 + 0.25 * 0.25
+    # an empty supply and an empty demand; supply 0 and demand 0 end together
+    C4 = np.full((3, 4), 0.5)
+    m, _ = O.fixup(C4, [0.25, 0.0, 0.75], [0.25, 0.25, 0.0, 0.5], 10.0, np.zeros((3, 4), np.int32))
+    assert np.array_equal(m, [[0.25, 0, 0, 0], [0, 0, 0, 0], [0, 0.25, 0, 0.5]])
+    # capacity runs out first: the last supply keeps its remainder
+    m, _ = O.fixup(np.full((3, 1), 0.5), [0.25, 0.5, 0.25], [0.5], 10.0, np.zeros((3, 1), np.int32))
+    assert np.array_equal(m, [[0.25], [0.25], [0.0]])
+
+
+def test_north_west_after_matched_and_trimmed_copies():
+    """Matched copies first (mass = count / theta), then the residuals.
+    theta = 4.  Diagonal copies: each pair holds 1/4 and the walk adds the
+    remaining 1/4 to the same pair.  Column 0 over-filled (2/4 + 1/4 > 1/2):
+    the excess 1/4 leaves the highest supplier, b = 1, whose remainder 1/2
+    then goes to column 1."""
+    C = np.array([[0.5, 0.25], [0.125, 0.75]])
+    m, _ = O.fixup(C, [0.5, 0.5], [0.5, 0.5], 4.0, np.array([[1, 0], [0, 1]], np.int32))
+    assert np.array_equal(m, [[0.5, 0], [0, 0.5]])
+    m, _ = O.fixup(C, [0.5, 0.5], [0.5, 0.5], 4.0, np.array([[2, 0], [1, 0]], np.int32))
+    assert np.array_equal(m, [[0.5, 0], [0, 0.5]])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_north_west_staircase_and_exact_units(seed):
+    """On random masses the walk's entries form a staircase (b and a never
+    decrease, one of them increases at each entry); on masses that are
+    multiples of 2^-40 every supply's row sums to its mass exactly (sums of
+    the FP64 entries taken in exact rational arithmetic)."""
+    from fractions import Fraction
+    g = np.random.Generator(np.random.PCG64(seed))
+    nB, nA = 37 + seed, 29 + 3 * seed
+    C = g.random((nB, nA))
+    z = np.zeros((nB, nA), np.int32)
+    nu, mu = g.exponential(size=nB), g.exponential(size=nA)
+    nu /= nu.sum()
+    mu /= mu.sum()
+    m, _ = O.fixup(C, nu, mu, 1.0, z)
+    bs, as_ = np.nonzero(m)  # row-major: b ascending, then a ascending
+    assert (np.diff(bs) >= 0).all() and (np.diff(as_) >= 0).all()
+    assert ((np.diff(bs) > 0) | (np.diff(as_) > 0)).all()
+    assert np.abs(m.sum(1) - nu).max() <= 1e-15 and (m.sum(0) - mu).max() <= 1e-15
+    q = lambda x: np.floor(x * 2.0 ** 40) / 2.0 ** 40
+    nu_d, mu_d = q(nu), q(mu)
+    mu_d[-1] += sum(Fraction(v) for v in nu_d) - sum(Fraction(v) for v in mu_d)  # equal totals
+    m, _ = O.fixup(C, nu_d, mu_d, 1.0, z)
+    for b in range(nB):
+        assert sum(Fraction(v) for v in m[b]) == Fraction(nu_d[b])
+    for a in range(nA):
+        assert sum(Fraction(v) for v in m[:, a]) == Fraction(mu_d[a])
+
+
+def test_counts_refuses_masses_that_do_not_sum_to_one():
+    """A mass of 2 or more, or a side summing to more than 1.5, is refused;
+    sums just below 1.5 pass."""
+    with pytest.raises(ValueError):
+        O.counts([1.0, 0.6], [0.8, 0.2], 0.5)
+    with pytest.raises(ValueError):
+        O.counts([0.5, 0.5], [0.5, 1.0], 0.5)
+    with pytest.raises(ValueError):
+        O.counts([2.0], [1.0], 0.5)
+    S, D = O.counts([0.75, 0.74], [1.0], 0.5)  # theta = 4 * 2 / 0.5 = 16
+    assert S.tolist() == [12, 11] and D.tolist() == [16]
