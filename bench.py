@@ -171,7 +171,6 @@ def src_hash():
     csrc = os.path.join(ROOT, "paper_2203_03732_gb300", "csrc")
     for f in PHASE_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "prot.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
