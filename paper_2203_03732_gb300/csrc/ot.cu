@@ -285,16 +285,22 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
                 }
                 const int lo = start - idx;
                 if (lo > 0) m &= lo >= W ? 0u : (kAll << lo) & kAll;
+                // every lane checks its lowest candidate's copies at once;
+                // the lowest lane with copies wins once no lower lane holds
+                // a candidate (lanes are in column order)
                 for (;;) {
-                    const unsigned any = __ballot_sync(0xFFFFFFFFu, m != 0);
-                    if (any == 0) break;
-                    const int L = __ffs(any) - 1;
-                    const int a = __shfl_sync(0xFFFFFFFFu, idx + __ffs(m) - 1, L);
-                    if (ld_relaxed_s32(p.avail + a) > 0) {
-                        found = a;
-                        break;
+                    if (__ballot_sync(0xFFFFFFFFu, m != 0) == 0) break;
+                    const int a_mine = idx + __ffs(m) - 1;
+                    const bool ok = m != 0 && ld_relaxed_s32(p.avail + a_mine) > 0;
+                    const unsigned okm = __ballot_sync(0xFFFFFFFFu, ok);
+                    if (!ok && m) m &= m - 1;
+                    if (okm) {
+                        const int L = __ffs(okm) - 1;
+                        if ((__ballot_sync(0xFFFFFFFFu, m != 0) & ((1u << L) - 1)) == 0) {
+                            found = __shfl_sync(0xFFFFFFFFu, a_mine, L);
+                            break;
+                        }
                     }
-                    if (lane == L) m &= m - 1;
                 }
             }
         }
@@ -394,7 +400,7 @@ __device__ __forceinline__ void ot_phase_end(const OParams &p) {
 // copy instance: T = floor(eps * S), S the total supply copies, the phase cap
 // S (2K + 3) / (T + 1) + 1 with K = floor(1/eps).
 template <class CB, bool F7>
-__global__ void __launch_bounds__(kOtThreads, 2) k_ot_loop(OParams p, double eps, long long spin_limit) {
+__global__ void __launch_bounds__(kOtThreads, 4) k_ot_loop(OParams p, double eps, long long spin_limit) {
     OCtl *c = p.ctl;
     // invalid masses or costs (recorded by the earlier kernels of the solve):
     // the copy counts are not all written, so no loop runs (every CTA reads
