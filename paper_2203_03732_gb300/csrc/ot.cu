@@ -61,7 +61,8 @@ namespace {
 constexpr int kOtThreads = 256;
 constexpr int kOtUnroll = 4;  // 2 KiB warp chunks (swept 3, 4, 8 at 10k x 10k)
 constexpr int kFlagSearching = 1, kFlagInBp = 2;
-constexpr int kFixUnroll = 8;  // plan-column chunks of 32 counts read at a time
+constexpr int kFixUnroll = 8;
+constexpr int kCostCtas = 64;  // CTAs of the cost sum (a constant: same order on every device)  // plan-column chunks of 32 counts read at a time
 
 struct OCtl {
     WsHead head;
@@ -73,6 +74,9 @@ struct OCtl {
     int pad;
     long long bytes;
     unsigned long long mass_units[2];  // sum of floor(m 2^32) over supplies, demands
+    unsigned cost_done;                // CTAs of k_fix_cost that have finished
+    unsigned pad2;
+    double cost_part[kCostCtas];       // their partial sums
 };
 
 struct OLayout {
@@ -474,13 +478,17 @@ struct FixParams {
 
 // Warp per demand a: nonzero count, the trim of its highest supplier, and the
 // remaining capacity q_a = max(0, mu_a - received), sums in ascending b.
+// The column's nonzero pairs are also compacted in place: the k-th (in
+// ascending b) leaves its b at lo[k] and its count at hi[k] of a's own plane
+// segments.  k <= b, and a warp writes only after it has read its whole group
+// of kFixUnroll chunks, so no count is overwritten before it is read.
 __global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
     const OParams &p = fp.o;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = warp_g; a < p.nA; a += nwarps) {
-        const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
+        int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
         int nnz = 0, last = -1;
         double recv = 0.0, before_last = 0.0, m_last = 0.0;
         for (int g0 = 0; g0 < p.nB; g0 += 32 * kFixUnroll) {
@@ -495,6 +503,11 @@ __global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
                 const int b0 = g0 + 32 * u, c = cs[u];
                 const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
                 if (!nz) continue;
+                if (c) {
+                    const int k = nnz + __popc(nz & ((1u << lane) - 1));
+                    lo[k] = b0 + lane;
+                    hi[k] = c;
+                }
                 nnz += __popc(nz);
                 const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
                 // lane order = ascending b: fold the chunk's masses in that order
@@ -528,17 +541,21 @@ __global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
     }
 }
 
-// One CTA: exclusive prefix sums of n counts (out[n] = total).
+// One CTA: exclusive prefix sums of n counts (out[n] = total); each thread
+// takes four consecutive counts per step.
 __global__ void k_prefix(const int *cnt, int n, int *out) {
     __shared__ int warp_tot[32];
     __shared__ int carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < n ? cnt[i] : 0;
-        int x = v;
+    for (int base = 0; base < n; base += 4 * blockDim.x) {
+        const int i0 = base + 4 * threadIdx.x;
+        int v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = i0 + e < n ? cnt[i0 + e] : 0;
+        const int own = v[0] + v[1] + v[2] + v[3];
+        int x = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -557,7 +574,12 @@ __global__ void k_prefix(const int *cnt, int n, int *out) {
             if (lane < nw) warp_tot[lane] = z - w;
         }
         __syncthreads();
-        if (i < n) out[i] = carry + warp_tot[warp] + x - v;
+        int run = carry + warp_tot[warp] + x - own;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (i0 + e < n) out[i0 + e] = run;
+            run += v[e];
+        }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry += warp_tot[warp] + x;
         __syncthreads();
@@ -565,42 +587,28 @@ __global__ void k_prefix(const int *cnt, int n, int *out) {
     if (threadIdx.x == 0) out[n] = carry;
 }
 
-// Warp per demand a: write a's plan entries (b ascending) at off_a[a]; count
-// the entries of every supply row.
+// Warp per demand a: write a's plan entries (b ascending) at off_a[a] from
+// the nnz_a[a] pairs that k_fix_demand compacted into a's plane segments;
+// count the entries of every supply row.
 __global__ void __launch_bounds__(kOtThreads) k_fix_write(FixParams fp) {
     const OParams &p = fp.o;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = warp_g; a < p.nA; a += nwarps) {
-        const int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
-        int pos = fp.off_a[a];
-        const int tb = fp.trim_b[a];
-        for (int g0 = 0; g0 < p.nB; g0 += 32 * kFixUnroll) {
-            int cs[kFixUnroll];
-#pragma unroll
-            for (int u = 0; u < kFixUnroll; ++u) {
-                const int b = g0 + 32 * u + lane;
-                cs[u] = b < p.nB ? lo[b] + hi[b] : 0;
+        const int *pb = lo_plane(p, a), *pc = hi_plane(p, a);
+        const int n = fp.nnz_a[a], base = fp.off_a[a], tb = fp.trim_b[a];
+        for (int i = lane; i < n; i += 32) {
+            const int b = pb[i];
+            double m = __ddiv_rn((double)pc[i], fp.theta);
+            if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
+            const long long k = (long long)base + i;
+            if (k < fp.plan_cap) {
+                fp.plan_row[k] = b;
+                fp.plan_col[k] = a;
+                fp.plan_mass[k] = m;
             }
-#pragma unroll
-            for (int u = 0; u < kFixUnroll; ++u) {
-                const int b = g0 + 32 * u + lane, c = cs[u];
-                const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
-                if (!nz) continue;
-                if (c) {
-                    const int k = pos + __popc(nz & ((1u << lane) - 1));
-                    double m = __ddiv_rn((double)c, fp.theta);
-                    if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
-                    if (k < fp.plan_cap) {
-                        fp.plan_row[k] = b;
-                        fp.plan_col[k] = a;
-                        fp.plan_mass[k] = m;
-                    }
-                    atomicAdd(fp.cnt_b + b, 1);
-                }
-                pos += __popc(nz);
-            }
+            atomicAdd(fp.cnt_b + b, 1);
         }
     }
 }
@@ -809,15 +817,20 @@ __global__ void k_fix_append(FixParams fp, OCtl *ctl, const int *flag, const int
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_extra = off[fp.o.nB + fp.o.nA];
 }
 
-// One CTA: cost = sum mass * c over the plan, fixed-order tree reduction.
+// cost = sum mass * c over the plan in a fixed order: kCostCtas CTAs each
+// take one contiguous share of the entries (a fixed tree inside the CTA); the
+// CTA that finishes last adds the kCostCtas partial sums in CTA order.
 template <class T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_fix_cost(FixParams fp, const T *C, long long ldc, OCtl *ctl, int64_t *plan_nnz, double *cost) {
-    __shared__ double part[1024];
+    __shared__ double part[256];
+    __shared__ bool last;
     const int nnz = fp.off_a[fp.o.nA] + ctl->n_extra;
     const int lim = nnz < fp.plan_cap ? nnz : (int)fp.plan_cap;
+    const int per = (lim + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int k0 = blockIdx.x * per, k1 = min(lim, k0 + per);
     double acc = 0.0;
-    for (int k = threadIdx.x; k < lim; k += blockDim.x)
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
         acc = __dadd_rn(acc, __dmul_rn(fp.plan_mass[k], (double)C[(long long)fp.plan_row[k] * ldc + fp.plan_col[k]]));
     part[threadIdx.x] = acc;
     __syncthreads();
@@ -826,7 +839,17 @@ k_fix_cost(FixParams fp, const T *C, long long ldc, OCtl *ctl, int64_t *plan_nnz
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *cost = part[0];
+        ctl->cost_part[blockIdx.x] = part[0];
+        __threadfence();
+        last = atomicAdd(&ctl->cost_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double *cp = ctl->cost_part;
+        double s = 0.0;
+        for (unsigned c = 0; c < gridDim.x; ++c) s = __dadd_rn(s, cp[c]);
+        *cost = s;
         *plan_nnz = nnz;
     }
 }
@@ -1030,9 +1053,9 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         PR_CUDA(cudaGetLastError());
     }
     if (dt == PR_F64)
-        k_fix_cost<double><<<1, 1024, 0, st>>>(fp, (const double *)C, ldc, p.ctl, plan_nnz, cost);
+        k_fix_cost<double><<<kCostCtas, 256, 0, st>>>(fp, (const double *)C, ldc, p.ctl, plan_nnz, cost);
     else
-        k_fix_cost<float><<<1, 1024, 0, st>>>(fp, (const float *)C, ldc, p.ctl, plan_nnz, cost);
+        k_fix_cost<float><<<kCostCtas, 256, 0, st>>>(fp, (const float *)C, ldc, p.ctl, plan_nnz, cost);
     PR_CUDA(cudaGetLastError());
     k_ot_duals<<<g1, 256, 0, st>>>(p, y_sup, dem_kmin, dem_lo, dem_hi);
     PR_CUDA(cudaGetLastError());
