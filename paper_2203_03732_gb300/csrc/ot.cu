@@ -323,23 +323,28 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
     return props;
 }
 
-// Warp per proposer: the winner of a takes g copies; the partners of matched
-// lo copies are evicted from the highest supply index down.
+// Thread per proposer: the winner of a takes g copies.  Grants that take
+// matched lo copies (kmin_a >= 1) go on a CTA list; after a CTA barrier each
+// warp evicts the partners of one listed grant, from the highest supply index
+// down.  Every a has one winner, and the counts other grants also touch (f)
+// change by atomics, so the order of the grants does not matter.  The CTA
+// walks its proposers in waves of blockDim.x, so the list never holds more
+// than blockDim.x grants.
 __device__ __forceinline__ void ot_grant(const OParams &p) {
-    const int lane = threadIdx.x & 31;
-    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int b = warp_g; b < p.nB; b += nwarps) {
-        const int a = p.pa[b];
-        if (a < 0) continue;
-        const bool win = row_of(p.prop[a]) == b;
-        int g = 0, need = 0;
-        if (lane == 0) {
+    __shared__ int ev_a[kOtThreads], ev_need[kOtThreads];
+    __shared__ int n_ev;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = blockIdx.x * blockDim.x; base < p.nB; base += gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) n_ev = 0;
+        __syncthreads();
+        const int b = base + threadIdx.x;
+        const int a = b < p.nB ? p.pa[b] : -1;
+        if (a >= 0) {
             p.pa[b] = -1;
-            if (win) {
+            if (row_of(p.prop[a]) == b) {
                 const int av = p.avail[a];
                 const int rb = p.r[b];
-                g = rb < av ? rb : av;
+                const int g = rb < av ? rb : av;
                 p.avail[a] = av - g;
                 p.r[b] = rb - g;
                 if (rb - g == 0) p.flag[b] &= ~kFlagSearching;
@@ -348,32 +353,39 @@ __device__ __forceinline__ void ot_grant(const OParams &p) {
                 p.granted[a] = 1;
                 hi_plane(p, a)[b] += g;
                 atomicSub(p.f + b, g);
-                need = p.kmin[a] >= 1 ? g : 0;
+                if (p.kmin[a] >= 1 && g > 0) {
+                    const int k = atomicAdd(&n_ev, 1);
+                    ev_a[k] = a;
+                    ev_need[k] = g;
+                }
             }
         }
-        need = __shfl_sync(0xFFFFFFFFu, need, 0);
-        if (need == 0) continue;
+        __syncthreads();
         // step (II): evict `need` lo-cluster partners, highest supply index first
-        int *lo = lo_plane(p, a);
-        for (int top = p.nB - 1; top >= 0 && need > 0; top -= 32) {
-            const int b2 = top - lane;
-            const int c = b2 >= 0 ? lo[b2] : 0;
-            int incl = c;
+        for (int e = warp; e < n_ev; e += nw) {
+            int *lo = lo_plane(p, ev_a[e]);
+            int need = ev_need[e];
+            for (int top = p.nB - 1; top >= 0 && need > 0; top -= 32) {
+                const int b2 = top - lane;
+                const int c = b2 >= 0 ? lo[b2] : 0;
+                int incl = c;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int before = incl - c;
+                int t = need - before;
+                t = t < 0 ? 0 : (t > c ? c : t);
+                if (t > 0) {
+                    lo[b2] = c - t;
+                    atomicAdd(p.f + b2, t);
+                }
+                const int chunk_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                need -= chunk_total < need ? chunk_total : need;
             }
-            const int before = incl - c;
-            int t = need - before;
-            t = t < 0 ? 0 : (t > c ? c : t);
-            if (t > 0) {
-                lo[b2] = c - t;
-                atomicAdd(p.f + b2, t);
-            }
-            const int chunk_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            need -= chunk_total < need ? chunk_total : need;
         }
+        __syncthreads();
     }
 }
 
