@@ -242,28 +242,36 @@ def run_reference(a, world, rank):
 
 
 def run_e2e(a, torch, prot, C_pin, Cd, ws, out, stream, ref):
-    """End to end from host memory: pinned host costs -> device (copy
-    engine), the solve, then the matching and the cost back to the host.
-    (The library also reads pinned host costs in place, which measured
-    slower than the copy: 14.5 vs 9-11 ms.)"""
+    """End to end from host memory through the public call: prot.assign on
+    the pinned host costs copies them to the device in row chunks, rounding
+    each chunk while the next is copied (pr_assign_staged), solves, and the
+    matching and the cost come back to the host.  One untimed call first, so
+    the device buffer's first allocation is not timed.  (The library also
+    reads pinned host costs in place, which measured slower than the copy
+    engines: 14.5 vs 9-11 ms.)"""
     r2c_host = torch.empty(a.n, dtype=torch.int32).pin_memory()
     cost_host = torch.empty((), dtype=torch.float64).pin_memory()
-    Cd2 = torch.empty_like(Cd)
     n_e2e = max(1, min(a.e2e_steps, a.steps))
+
+    def step():
+        prot.assign(C_pin, a.eps, ws=ws, sync=False, out=out, results_on_device=True)
+        r2c_host.copy_(out["row_to_col"], non_blocking=True)
+        cost_host.copy_(out["cost"], non_blocking=True)
+
+    step()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(n_e2e):
-        Cd2.copy_(C_pin, non_blocking=True)
-        prot.assign(Cd2, a.eps, ws=ws, sync=False, out=out)
-        r2c_host.copy_(out["row_to_col"], non_blocking=True)
-        cost_host.copy_(out["cost"], non_blocking=True)
+        step()
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / n_e2e
     assert float(cost_host) == float(ref["cost"].cpu())
+    assert torch.equal(r2c_host, ref["row_to_col"].cpu())
     return {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Cd.numel() * 8),
-            "d2h_bytes_per_step": int(a.n * 4 + 8)}
+            "d2h_bytes_per_step": int(a.n * 4 + 8),
+            "path": "prot.assign on pinned host costs (pr_assign_staged: chunked copy, rounding overlapped)"}
 
 
 def timed(torch, stream, fn, reps):

@@ -131,6 +131,33 @@ pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, 
                          size_t ws_bytes, void *stream);
 
 /*
+ * pr_assign_staged -- pr_assign for a cost matrix in host memory: the
+ * rounding of Eq. 1 overlaps the host-to-device copy.  The rows of C_host go
+ * to C_dev in chunks of about 32 MB on a copy stream the library owns (one
+ * per device, made on first use), and each chunk is rounded on `stream` as
+ * soon as it has arrived, while the next one is being copied; the phase loop
+ * then runs as in pr_assign.  The results equal pr_assign(C_dev, ...) bit for
+ * bit.
+ *
+ *   C_host  n_rows x n_cols costs in [0,1] (FP32/FP64), row pitch ldc, host
+ *           memory; page-locked (pinned) memory lets the copies run
+ *           asynchronously, pageable memory works but each copy then waits
+ *           for the host
+ *   C_dev   device buffer of the same layout (n_rows rows of pitch ldc), owned
+ *           by the caller; it holds the copied costs afterwards (the cost of
+ *           the matching is read from it)
+ *   other arguments as pr_assign
+ * The copy stream first waits for the work already enqueued on `stream`.
+ * Enqueueing is serialised across host threads by a library mutex.  Errors
+ * as pr_assign; PR_ERR_INVALID also when C_host is not host memory or C_dev
+ * not device memory.
+ */
+pr_status pr_assign_staged(const void *C_host, void *C_dev, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                           int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
+                           int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/*
  * pr_dual_bound -- the a-posteriori certificate of a pr_assign solve
  * (Lemma 3.1).  The duals it returns satisfy Eq. (2), y(a) + y(b) <= cbar +
  * eps on every edge; summed over any matching that covers the rows (column

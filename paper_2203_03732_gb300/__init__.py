@@ -67,8 +67,9 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
 
     C: (n_rows, n_cols) float32/float64 tensor with costs in [0, 1],
        n_rows <= n_cols.  A CUDA tensor is solved in place on its device; a
-       CPU tensor is copied to the current CUDA device (the copy engines move
-       it faster than the kernels read pinned host memory in place) and the
+       CPU tensor (pinned memory for asynchronous copies) is copied to the
+       current CUDA device in row chunks, each chunk rounded while the next
+       is copied (pr_assign_staged; rule "offset" copies first), and the
        results are copied back (the end-to-end path).
     Returns a dict: row_to_col, col_to_row (int32), y_row, y_col (int32 duals
     in units of eps), cost (float64 scalar tensor) and, when sync, stats.
@@ -81,12 +82,17 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
     L = _lib.load()
     host_in = not C.is_cuda
     dev = torch.device("cuda", torch.cuda.current_device()) if host_in else C.device
-    if host_in:
+    if C.dim() != 2:
+        raise ValueError("C must be 2-D")
+    staged = host_in and rule == "lowest"
+    if staged:
+        if C.stride(1) != 1:
+            C = C.contiguous()
+        Cd = torch.empty_strided(C.shape, C.stride(), dtype=C.dtype, device=dev)
+    elif host_in:
         Cd = C.to(dev, non_blocking=True)
     else:
         Cd = C
-    if Cd.dim() != 2:
-        raise ValueError("C must be 2-D")
     if Cd.stride(1) != 1:
         Cd = Cd.contiguous()
     if Cd.dtype == torch.float64:
@@ -114,7 +120,9 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
             out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["cost"].data_ptr(),
             ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
             _stream_handle(torch, dev))
-    if rule == "lowest":
+    if staged:
+        rc = L.pr_assign_staged(C.data_ptr(), *args)
+    elif rule == "lowest":
         rc = L.pr_assign(*args)
     elif rule == "offset":
         rc = L.pr_assign_rule(_lib.PR_RULE_OFFSET, *args)

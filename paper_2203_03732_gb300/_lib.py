@@ -92,6 +92,8 @@ SIGNATURES = {
     "pr_dual_bound": (ctypes.c_int, [_vp, _vp, _i32, _i32, _dbl, _vp, _vp, _vp]),
     "pr_assign_rule": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp,
                                       _vp, _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
+    "pr_assign_staged": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
+                                        _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_assign_points": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _i32, _i32, _dbl, _vp, _vp, _vp, _vp,
                                         _vp, ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_ws_status": (ctypes.c_int, [_vp, _vp]),

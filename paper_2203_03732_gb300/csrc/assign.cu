@@ -1323,9 +1323,11 @@ bool use_slots_in_grid(int nslots) {
 }
 
 // Where the costs come from: a matrix (C, dt, ldc) or two point sets (XA the
-// columns, XB the rows, `dim` FP32 coordinates each).
+// columns, XB the rows, `dim` FP32 coordinates each).  With `host` set, the
+// matrix is in host memory and C is the device buffer it is copied into.
 struct CostSource {
     const void *C = nullptr;
+    const void *host = nullptr;
     pr_dtype dt = PR_F64;
     int64_t ldc = 0;
     const float *XA = nullptr, *XB = nullptr;
@@ -1344,6 +1346,73 @@ void launch_points(const CostSource &src, int n_rows, int n_cols, const Params &
     else
         k_points_quant<uint16_t, D><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, n_rows, n_cols,
                                                            p.ldq, &p.ctl->maxbits, e, (uint16_t *)cbw, &p.ctl->head);
+}
+
+// pr_assign_staged's copy stream and chunk events, one set per device, made
+// on first use and kept.  A solve enqueues its whole copy and rounding
+// sequence under g_stage_mu, so no other solve re-records an event between
+// its record and the wait that pairs with it.
+constexpr size_t kStageBytes = (size_t)32 << 20;  // host bytes per chunk
+constexpr int kStageMaxChunks = 64;
+constexpr int kStageMaxDevices = 64;
+struct StageRes {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr;
+    cudaEvent_t done[kStageMaxChunks] = {};
+};
+std::mutex g_stage_mu;
+StageRes g_stage[kStageMaxDevices];
+
+template <class T, class CB>
+void launch_quantise_rows(const CostSource &src, const Params &p, int r0, int rows, double eps, int sms,
+                          cudaStream_t st) {
+    const long long groups = (long long)rows * (p.ldq >> 3);
+    const long long want = groups / 256 + 1;
+    const int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
+    launch_quantise<T, CB>((const T *)src.C + (size_t)r0 * src.ldc, src.ldc, rows, p.nA, p.ldq, eps,
+                           (CB *)const_cast<void *>(p.cb) + (size_t)r0 * p.ldq, &p.ctl->head, grid, st);
+}
+
+// Eq. 1 for a host matrix: its rows go to the device buffer src.C in chunks
+// of about kStageBytes on the copy stream, and each chunk is rounded on `st`
+// as soon as it has arrived, while the next chunk is being copied.  The copy
+// stream first waits for the work already on `st`, so a buffer that earlier
+// work on `st` still reads is not overwritten early.
+pr_status stage_and_round(const CostSource &src, const Params &p, double eps, bool cb8, cudaStream_t st) {
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStageMaxDevices) return fail(PR_ERR_INVALID, "pr_assign_staged: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    StageRes &R = g_stage[dev];
+    if (!R.copy) {
+        PR_CUDA(cudaStreamCreateWithFlags(&R.copy, cudaStreamNonBlocking));
+        PR_CUDA(cudaEventCreateWithFlags(&R.start, cudaEventDisableTiming));
+        for (int k = 0; k < kStageMaxChunks; ++k)
+            PR_CUDA(cudaEventCreateWithFlags(&R.done[k], cudaEventDisableTiming));
+    }
+    const size_t esz = src.dt == PR_F64 ? 8 : 4;
+    const int n_rows = p.nB, n_cols = p.nA;
+    const size_t row_bytes = (size_t)n_cols * esz;
+    int rows_per = (int)std::max<size_t>(1, kStageBytes / row_bytes);
+    if ((n_rows + rows_per - 1) / rows_per > kStageMaxChunks) rows_per = (n_rows + kStageMaxChunks - 1) / kStageMaxChunks;
+    const int sms = device_info().sms;
+    PR_CUDA(cudaEventRecord(R.start, st));
+    PR_CUDA(cudaStreamWaitEvent(R.copy, R.start, 0));
+    const size_t pitch = (size_t)src.ldc * esz;
+    for (int k = 0, r0 = 0; r0 < n_rows; ++k, r0 += rows_per) {
+        const int rows = std::min(rows_per, n_rows - r0);
+        PR_CUDA(cudaMemcpy2DAsync((char *)const_cast<void *>(src.C) + (size_t)r0 * pitch, pitch,
+                                  (const char *)src.host + (size_t)r0 * pitch, pitch, row_bytes, rows,
+                                  cudaMemcpyHostToDevice, R.copy));
+        PR_CUDA(cudaEventRecord(R.done[k], R.copy));
+        PR_CUDA(cudaStreamWaitEvent(st, R.done[k], 0));
+        if (src.dt == PR_F64 && cb8) launch_quantise_rows<double, uint8_t>(src, p, r0, rows, eps, sms, st);
+        else if (src.dt == PR_F64) launch_quantise_rows<double, uint16_t>(src, p, r0, rows, eps, sms, st);
+        else if (cb8) launch_quantise_rows<float, uint8_t>(src, p, r0, rows, eps, sms, st);
+        else launch_quantise_rows<float, uint16_t>(src, p, r0, rows, eps, sms, st);
+        PR_CUDA(cudaGetLastError());
+    }
+    return PR_OK;
 }
 
 // Everything after the argument checks, shared by pr_assign, pr_assign_points
@@ -1383,6 +1452,9 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
         if (D == 2) launch_points<2>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
         else if (D == 3) launch_points<3>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
         else launch_points<0>(src, n_rows, n_cols, p, e, cb8, cbw, qgrid, st);
+    } else if (src.host) {
+        const pr_status rc = stage_and_round(src, p, eps, cb8, st);
+        if (rc != PR_OK) return rc;
     } else if (dt == PR_F64 && cb8)
         launch_quantise<double, uint8_t>((const double *)C, ldc, n_rows, n_cols, p.ldq, eps, (uint8_t *)cbw,
                                          &p.ctl->head, qgrid, st);
@@ -1592,6 +1664,32 @@ extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, in
     src.ldc = ldc;
     return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
                          ws_bytes, stream, "pr_assign_rule", (int)rule);
+}
+
+extern "C" pr_status pr_assign_staged(const void *C_host, void *C_dev, pr_dtype dt, int64_t ldc, int32_t n_rows,
+                                      int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
+                                      int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
+                                      size_t ws_bytes, void *stream) {
+    if (!C_host || !C_dev) return fail(PR_ERR_INVALID, "pr_assign_staged: NULL pointer argument");
+    if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_staged: bad dtype");
+    if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_staged: ldc < n_cols");
+    cudaPointerAttributes ah, ad;
+    if (cudaPointerGetAttributes(&ah, C_host) != cudaSuccess ||
+        cudaPointerGetAttributes(&ad, C_dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PR_ERR_INVALID, "pr_assign_staged: a pointer the CUDA runtime does not know");
+    }
+    if (ah.type != cudaMemoryTypeHost && ah.type != cudaMemoryTypeUnregistered)
+        return fail(PR_ERR_INVALID, "pr_assign_staged: C_host must be host memory");
+    if (ad.type != cudaMemoryTypeDevice)
+        return fail(PR_ERR_INVALID, "pr_assign_staged: C_dev must be device memory");
+    CostSource src;
+    src.C = C_dev;
+    src.host = C_host;
+    src.dt = dt;
+    src.ldc = ldc;
+    return assign_common(src, n_rows, n_cols, eps, row_to_col, col_to_row, y_row, y_col, cost, stats, ws,
+                         ws_bytes, stream, "pr_assign_staged");
 }
 
 extern "C" pr_status pr_assign_points(const float *XA, const float *XB, int32_t dim, pr_metric metric,
