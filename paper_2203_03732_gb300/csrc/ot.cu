@@ -264,12 +264,25 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const CB *key = static_cast<const CB *>(p.key);
     unsigned long long bytes = 0;
+    // a row's flag, dual and resume column are loaded together, and the next
+    // row's while this one is scanned (only this warp writes them here)
+    int nfl = 0, nF = 0, nst = 0;
+    if (warp_g < p.nB) {
+        nfl = p.flag[warp_g];
+        nF = p.F[warp_g];
+        nst = p.ptr[warp_g];
+    }
     for (int b = warp_g; b < p.nB; b += nwarps) {
-        if (!(p.flag[b] & kFlagSearching)) continue;
-        const uint32_t tgt = (uint32_t)(p.F[b] - 1);
+        const int fl = nfl, Fb = nF, start = nst;
+        if (b + nwarps < p.nB) {
+            nfl = p.flag[b + nwarps];
+            nF = p.F[b + nwarps];
+            nst = p.ptr[b + nwarps];
+        }
+        if (!(fl & kFlagSearching)) continue;
+        const uint32_t tgt = (uint32_t)(Fb - 1);
         const uint32_t t2 = W == 8 ? (tgt | (tgt << 16)) : tgt * 0x01010101u;
         const CB *row = static_cast<const CB *>(p.cb) + (size_t)b * p.ldq;
-        const int start = p.ptr[b];
         int found = -1;
         for (int c0 = start & ~(W - 1); c0 < p.ldq && found < 0; c0 += kChunkW) {
             uint4 cv[kOtUnroll];
@@ -341,9 +354,14 @@ __device__ __forceinline__ void ot_grant(const OParams &p) {
         const int a = b < p.nB ? p.pa[b] : -1;
         if (a >= 0) {
             p.pa[b] = -1;
-            if (row_of(p.prop[a]) == b) {
-                const int av = p.avail[a];
-                const int rb = p.r[b];
+            // the winner test and the values a winner needs, loaded at once
+            // (only a's winner writes them in this step)
+            const unsigned long long w = p.prop[a];
+            const int av = p.avail[a];
+            const int rb = p.r[b];
+            const int km = p.kmin[a];
+            int *hp = hi_plane(p, a) + b;
+            if (row_of(w) == b) {
                 const int g = rb < av ? rb : av;
                 p.avail[a] = av - g;
                 p.r[b] = rb - g;
@@ -351,9 +369,9 @@ __device__ __forceinline__ void ot_grant(const OParams &p) {
                 p.clo[a] -= g;
                 p.chi[a] += g;
                 p.granted[a] = 1;
-                hi_plane(p, a)[b] += g;
+                *hp += g;
                 atomicSub(p.f + b, g);
-                if (p.kmin[a] >= 1 && g > 0) {
+                if (km >= 1 && g > 0) {
                     const int k = atomicAdd(&n_ev, 1);
                     ev_a[k] = a;
                     ev_need[k] = g;
