@@ -16,7 +16,9 @@
 // a's matches at key kmin_a (its "lo" cluster), the other plane those at
 // kmin_a + 1.  When the lo cluster runs out (every match in it was evicted,
 // or it held a's free copies) the planes swap roles: the emptied plane is
-// all zero and becomes the new "hi" plane.
+// all zero and becomes the new "hi" plane.  After the loop, k_fix_demand
+// reads each column's two segments once and compacts its nonzero (b, count)
+// pairs into their heads; k_fix_write reads only those.
 //
 // One phase (B' = supply vertices with free copies), steps of k_ot_loop (one
 // cooperative launch; a grid barrier with a summed payload after each step):
