@@ -10,7 +10,10 @@
  *     space is the caller's workspace `ws` of at least the bytes returned by
  *     the matching *_workspace() query, 256-byte aligned.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *     stream).  Work is enqueued on it in order; nothing else is touched.
+ *     stream).  Work is enqueued on it in order; nothing else is touched,
+ *     except by pr_assign_staged, whose host-to-device copies run on a copy
+ *     stream of the library's own (ordered after the work already on
+ *     `stream`; see there).
  *   - Rows are the supply side B (the side whose free vertices propose, the
  *     set B' of Sec. 2.2); columns are the demand side A.  Costs are row-major
  *     with leading dimension `ldc` (elements).  The paper assumes the costs are
