@@ -121,6 +121,19 @@ def test_ot_uniform_masses(prot, nB, nA, eps):
     assert (dense.sum(0) - mu).max() <= 1e-12
 
 
+@pytest.mark.parametrize("nB,nA,eps", [(1, 300, 0.1), (300, 1, 0.1), (2, 700, 0.05), (700, 3, 0.2)])
+def test_ot_one_or_few_vertices_on_a_side(prot, nB, nA, eps):
+    """Degenerate shapes: one supply vertex (its copies spread over every
+    demand), one demand vertex (one winner per round), and two or three
+    vertices on a side; the north-west prefix sums then have one to three
+    entries on that side."""
+    C, nu, mu = W.ot_euclid_2d(nB, nA, 21)
+    r, dense = gpu_ot(prot, C, nu, mu, eps)
+    assert_ot_parity(r, dense, O.ot(C, nu, mu, eps))
+    assert np.abs(dense.sum(1) - nu).max() <= 1e-12
+    assert (dense.sum(0) - mu).max() <= 1e-12
+
+
 def test_ot_barrier_timeout_reported_not_hung(prot, monkeypatch):
     """The loop kernel's grid barriers wait at most PR_SPIN_LIMIT_CYCLES: with
     one cycle every CTA gives up at its first barrier, pr_ot returns
