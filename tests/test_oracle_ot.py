@@ -263,3 +263,27 @@ def test_cluster_and_expanded_forms_mostly_agree():
             agree += (r["stats"]["phases"] == e["phases"]
                       and np.array_equal(r["plan_lo"] + r["plan_hi"], e["counts"]))
     assert agree >= 100
+
+
+@pytest.mark.parametrize("n,eps,seed", [(64, 0.5, 0), (128, 0.25, 2), (32, 0.125, 4), (16, 0.0625, 5),
+                                        (64, 0.03125, 6)])
+def test_one_copy_per_vertex_is_the_assignment_solve(n, eps, seed):
+    """Masses 1/theta (theta = 4n/eps a power of two, so they are exact):
+    every vertex is one copy, the cluster phases are Sec. 2.2's, and the
+    fix-up routes the free supplies' masses north-west, i.e. the k-th free
+    row to the k-th free column, which is the assignment's completion.  The
+    whole OT solve then equals the assignment solve: plan = permutation /
+    theta, the same duals, phases and rounds, cost / theta."""
+    th = O.theta(n, n, eps)
+    assert th == 2.0 ** round(np.log2(th))
+    C = W.assignment_euclid_2d(n, seed)
+    nu = np.full(n, 1.0 / th)
+    r = O.ot(C, nu, nu.copy(), eps)
+    a = oracle.assign(C, eps)
+    assert set(r["S"].tolist()) == {1} and set(r["D"].tolist()) == {1}
+    plan = np.zeros((n, n))
+    plan[np.arange(n), a["row_to_col"]] = 1.0 / th
+    assert np.array_equal(r["mass"], plan)
+    assert np.array_equal(r["F"], a["y_row"]) and np.array_equal(-r["kmin"], a["y_col"])
+    assert r["stats"]["phases"] == a["stats"]["phases"] and r["stats"]["rounds"] == a["stats"]["rounds"]
+    assert abs(r["cost"] * th - a["cost"]) <= 1e-12 * a["cost"]
