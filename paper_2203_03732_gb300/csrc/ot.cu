@@ -51,7 +51,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "prot_internal.cuh"
 #include "quantise.cuh"
