@@ -63,6 +63,46 @@ def test_host_argument_errors_without_gpu(libpath):
     assert b"NULL" in L.pr_last_error()
 
 
+def test_staged_and_ot_argument_errors_without_gpu(libpath):
+    """pr_assign_staged and pr_ot check their arguments on the host before
+    any CUDA call: each bad argument returns PR_ERR_INVALID with a message."""
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load(libpath)
+    buf = ctypes.create_string_buffer(4096)
+    p = ctypes.cast(buf, ctypes.c_void_p).value
+    outs = (p, p, p, p, p)
+    cases = [
+        ((None, p, 1, 10, 10, 10, 0.1), b"NULL"),
+        ((p, None, 1, 10, 10, 10, 0.1), b"NULL"),
+        ((p, p, 7, 10, 10, 10, 0.1), b"dtype"),
+        ((p, p, 1, 9, 10, 10, 0.1), b"ldc"),
+    ]
+    for head, msg in cases:
+        rc = L.pr_assign_staged(*head, *outs, None, p, 4096, None)
+        assert rc == _lib.PR_ERR_INVALID
+        assert msg in L.pr_last_error()
+    f64 = (ctypes.c_double * 4)()
+    dp = ctypes.cast(f64, ctypes.c_void_p).value
+    ot_cases = [
+        (dict(C=None), b"NULL"),
+        (dict(dt=7), b"dtype"),
+        (dict(n_sup=0), b"n_sup"),
+        (dict(ldc=1), b"ldc"),
+        (dict(eps=1.5), b"eps"),
+        (dict(eps=1e-6), b"eps"),
+        (dict(plan_cap=0), b"plan_cap"),
+        (dict(ws=None), b"workspace"),
+    ]
+    for change, msg in ot_cases:
+        a = dict(C=p, dt=1, ldc=4, n_sup=2, n_dem=2, supply=dp, demand=dp, eps=0.1, plan_cap=8, ws=p)
+        a.update(change)
+        rc = L.pr_ot(a["C"], a["dt"], a["ldc"], a["n_sup"], a["n_dem"], a["supply"], a["demand"], a["eps"],
+                     a["plan_cap"], p, p, p, p, p, p, p, p, p, None, a["ws"], 1 if a["ws"] else 0, None)
+        expect = _lib.PR_ERR_WORKSPACE if msg == b"workspace" else _lib.PR_ERR_INVALID
+        assert rc == expect, (change, rc)
+        assert msg in L.pr_last_error(), (change, L.pr_last_error())
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2203_03732_gb300 import _lib
     saved = _lib._lib
