@@ -103,6 +103,48 @@ def test_staged_and_ot_argument_errors_without_gpu(libpath):
         assert msg in L.pr_last_error(), (change, L.pr_last_error())
 
 
+def test_other_entry_points_argument_errors_without_gpu(libpath):
+    """The host-side argument checks of the remaining entry points, each
+    before any CUDA call: PR_ERR_INVALID and a message naming the argument."""
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load(libpath)
+    buf = ctypes.create_string_buffer(4096)
+    p = ctypes.cast(buf, ctypes.c_void_p).value
+    n_host = (ctypes.c_int32 * 2)(64, 64)
+    calls = [
+        (lambda: L.pr_assign_rule(5, p, 1, 10, 10, 10, 0.1, p, p, p, p, p, None, p, 4096, None), b"rule"),
+        (lambda: L.pr_assign_points(None, p, 2, 1, 10, 10, 0.1, p, p, p, p, p, None, p, 4096, None), b"NULL"),
+        (lambda: L.pr_assign_points(p, p, 0, 1, 10, 10, 0.1, p, p, p, p, p, None, p, 4096, None), b"dim"),
+        (lambda: L.pr_assign_points(p, p, 2, 9, 10, 10, 0.1, p, p, p, p, p, None, p, 4096, None), b"metric"),
+        (lambda: L.pr_assign_points(p, p, 2, 1, 11, 10, 0.1, p, p, p, p, p, None, p, 4096, None), b"n_rows"),
+        (lambda: L.pr_assign_points(p, p, 2, 1, 10, 10, 0.0, p, p, p, p, p, None, p, 4096, None), b"eps"),
+        (lambda: L.pr_assign_batched(None, 1, 2, n_host, 0.1, p, p, p, p, p, p, None, None, p, 4096, None),
+         b"NULL"),
+        (lambda: L.pr_assign_batched(p, 7, 2, n_host, 0.1, p, p, p, p, p, p, None, None, p, 4096, None),
+         b"dtype"),
+        (lambda: L.pr_assign_batched_points(None, p, 3, 0, 2, n_host, 0.1, p, p, p, p, p, p, None, None, p,
+                                            4096, None), b"NULL"),
+        (lambda: L.pr_assign_batched_points(p, p, 0, 0, 2, n_host, 0.1, p, p, p, p, p, p, None, None, p,
+                                            4096, None), b"dim"),
+        (lambda: L.pr_assign_batched_points(p, p, 3, 9, 2, n_host, 0.1, p, p, p, p, p, p, None, None, p,
+                                            4096, None), b"metric"),
+        (lambda: L.pr_assign_backward(None, p, p, 1, 8, 3, p, p, p, None, None), b"NULL"),
+        (lambda: L.pr_assign_backward(p, p, p, 0, 8, 3, p, p, p, None, None), b"batch"),
+        (lambda: L.pr_assign_backward(p, p, p, 1, 8, 5000, p, p, p, None, None), b"dim"),
+        (lambda: L.pr_dual_bound(None, p, 4, 4, 0.1, p, p, None), b"NULL"),
+        (lambda: L.pr_dual_bound(p, p, 5, 4, 0.1, p, p, None), b"n_rows"),
+        (lambda: L.pr_dual_bound(p, p, 4, 4, 1.0, p, p, None), b"eps"),
+        (lambda: L.pr_assign_noalloc(None, 1, 10, 10, 10, 0.1, p, p, p, p, p, None, None), b"NULL"),
+        (lambda: L.pr_assign_noalloc(p, 7, 10, 10, 10, 0.1, p, p, p, p, p, None, None), b"dtype"),
+        (lambda: L.pr_assign_noalloc(p, 1, 2000, 2000, 2000, 0.1, p, p, p, p, p, None, None), b"1024"),
+        (lambda: L.pr_assign_noalloc(p, 1, 9, 10, 10, 0.1, p, p, p, p, p, None, None), b"ldc"),
+        (lambda: L.pr_assign_noalloc(p, 1, 10, 10, 10, 2.0, p, p, p, p, p, None, None), b"eps"),
+    ]
+    for call, msg in calls:
+        assert call() == _lib.PR_ERR_INVALID, msg
+        assert msg in L.pr_last_error(), (msg, L.pr_last_error())
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2203_03732_gb300 import _lib
     saved = _lib._lib
