@@ -287,3 +287,35 @@ def test_one_copy_per_vertex_is_the_assignment_solve(n, eps, seed):
     assert np.array_equal(r["F"], a["y_row"]) and np.array_equal(-r["kmin"], a["y_col"])
     assert r["stats"]["phases"] == a["stats"]["phases"] and r["stats"]["rounds"] == a["stats"]["rounds"]
     assert abs(r["cost"] * th - a["cost"]) <= 1e-12 * a["cost"]
+
+
+def test_copy_checker_catches_planted_mistakes():
+    """The expanded form's checker is not vacuous: a matched pair off by one
+    in its dual sum, a demand copy's dual raised above 0, a free supply copy
+    below its siblings' dual, and a non-matched pair over cbar + 1 are each
+    reported."""
+    import copy
+    from oracle.ot_expanded import copy_violations, ot_expanded
+    C, nu, mu = W.ot_euclid_2d(4, 3, 1)
+    eps = 0.4
+    cb = oracle.quantise(C, eps)
+    S, D = O.counts(nu, mu, eps)
+    T = int(np.floor(eps * S.sum()))
+    e = ot_expanded(cb, S, D, T)
+    assert copy_violations(e, cb) == 0
+    i = next(k for k, j in enumerate(e["match"]) if j >= 0)
+    bad = copy.deepcopy(e)
+    bad["y_sup"][i] += 1  # matched pair: sum no longer cbar
+    assert copy_violations(bad, cb) > 0
+    bad = copy.deepcopy(e)
+    bad["y_dem"][e["match"][i]] = 1  # a demand dual above 0
+    assert copy_violations(bad, cb) > 0
+    free = [k for k, j in enumerate(e["match"]) if j < 0]
+    if free:
+        bad = copy.deepcopy(e)
+        bad["y_sup"][free[0]] -= 1  # below its siblings (raise invariant)
+        assert copy_violations(bad, cb) > 0
+    bad = copy.deepcopy(e)
+    j0 = next(j for j in range(len(e["dem"])) if j != e["match"][i])
+    bad["y_dem"][j0] = cb[e["sup"][i]][e["dem"][j0]] + 2 - bad["y_sup"][i]  # over cbar + 1
+    assert copy_violations(bad, cb) > 0
