@@ -482,3 +482,34 @@ def test_parallel_scans_change_nothing(mode):
         for k in ("row_to_col", "col_to_row", "y_row", "y_col"):
             assert np.array_equal(r0[k], r1[k])
         assert r0["stats"] == r1["stats"] and r0["cost"] == r1["cost"]
+
+
+def test_state_checker_catches_planted_mistakes():
+    """or_check_state (behind the per-phase invariant mode) is not vacuous:
+    a final state passes, and each planted mistake is reported: a matched
+    pair whose duals no longer sum to cbar (Eq. 3), a pair over cbar + 1
+    (Eq. 2), a negative row dual or a free column with a nonzero dual (I1),
+    and match arrays that disagree."""
+    C = W.assignment_euclid_2d(30, 3)
+    eps = 0.1
+    cb = oracle.quantise(C, eps)
+    r = oracle.assign_int(cb, oracle.threshold(eps, 30))
+    mb, ma, yb, ya = (r[k].copy() for k in ("match_b", "match_a", "y_b", "y_a"))
+    assert oracle.check_state(cb, mb, ma, yb, ya) == 0
+    b = int(np.flatnonzero(mb >= 0)[0])
+    a = int(mb[b])
+
+    def bad(**kw):
+        s = dict(match_b=mb.copy(), match_a=ma.copy(), y_b=yb.copy(), y_a=ya.copy())
+        for k, f in kw.items():
+            f(s[k])
+        return oracle.check_state(cb, s["match_b"], s["match_a"], s["y_b"], s["y_a"])
+
+    assert bad(y_b=lambda v: v.__setitem__(b, v[b] + 1)) > 0
+    a2 = next(x for x in range(cb.shape[1]) if x != a)
+    assert bad(y_a=lambda v: v.__setitem__(a2, cb[b, a2] + 2 - yb[b])) > 0
+    assert bad(y_b=lambda v: v.__setitem__(b, -1)) > 0
+    free_a = np.flatnonzero(ma < 0)
+    if free_a.size:
+        assert bad(y_a=lambda v: v.__setitem__(int(free_a[0]), -1)) > 0
+    assert bad(match_a=lambda v: v.__setitem__(a, -1)) > 0
