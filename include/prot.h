@@ -364,13 +364,19 @@ pr_status pr_assign_backward(const int32_t *row_to_col, const float *X, const fl
  * Instead of a caller workspace it uses one device array of 2.25 MiB built
  * into the library; every GPU that loads the library holds that array until
  * the process exits.  Limits: n_rows <= n_cols <= 1024 (larger sizes return
- * PR_ERR_INVALID with a message).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  All calls on a device
- * share the array and each call reinitialises what it uses, so calls that
- * overlap on the GPU (other streams, other host threads) race: serialise
- * them.  No memory is allocated or freed by this call.  Other arguments and
- * errors as pr_assign (stats non-NULL makes the call synchronous).
+ * PR_ERR_INVALID with a message).  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, with the call's device current), and the
+ * first call on a device is also where the runtime loads the library's
+ * kernels on it: make that first call before any stream capture.  All calls
+ * on a device share the array and each call reinitialises what it uses, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  No memory is allocated or freed by this call.  C is
+ * checked as in pr_assign (device, managed or pinned host memory; other host
+ * memory is refused with PR_ERR_INVALID before anything is enqueued).  Other
+ * arguments and errors as pr_assign, with one difference: a device-side
+ * error (a spin-limit time-out, an internal check) is returned only when
+ * stats != NULL, which makes the call synchronous; with stats == NULL such
+ * an error goes unreported, since the array's status word has no query.
  */
 pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int32_t n_cols,
                             double eps, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,

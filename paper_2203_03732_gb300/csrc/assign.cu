@@ -3,7 +3,7 @@
 // Pipeline (all on the caller's stream, no host round trip inside a solve):
 //   k_init      y(b) = 1, y(a) = 0, M empty                        (Sec. 2.2)
 //   k_quantise  cbar = floor(c / eps) exactly, [b][a]: uint8 when
-//               floor(1/eps) <= 254, else uint16                   (Eq. 1)
+//               floor(1/eps) <= 252, else uint16                   (Eq. 1)
 //   k_phases    persistent cooperative kernel: every phase and round
 //   k_decode    matching and y(A) out of the per-column words
 //   k_finish    completion + FP64 cost                             (Sec. 2.1)
@@ -12,7 +12,7 @@
 // (slack 0, Eq. 2 with equality) iff  cbar(b,a) + k(a) == y(b) - 1.  Both
 // cbar and k fit 16 bits (Lemma 3.2 bounds |y| by floor(1/eps) + 2), so one
 // 16-byte load of eight cbar values meets eight k values in four 32-bit adds
-// (two 16-bit lanes per word, no carry between them).  When cbar <= 254 it is
+// (two 16-bit lanes per word, no carry between them).  When cbar <= 252 it is
 // stored in one byte: the matrix is half the size (100 MB at n = 10,000,
 // inside the 126 MB L2, so the later phases' rescans hit L2 instead of HBM),
 // and each 16-byte load brings sixteen values, widened to 16-bit lanes.
@@ -1749,24 +1749,14 @@ NoAllocLayout make_noalloc_layout(int nB, int nA) {
     return L;
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (cudaGetSymbolAddress must run with that device current).
+// Device address of the scratch array for the current device.  It is looked
+// up on every call (cudaGetSymbolAddress must run with that device current;
+// it allocates nothing), so no address outlives a reload of the module.
 pr_status noalloc_scratch(char **out) {
-    static char *addr[64];
-    static bool ready[64];
-    static std::mutex mu;
-    int dev = 0;
-    PR_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(PR_ERR_INVALID, "pr_assign_noalloc: device ordinal %d too large", dev);
-    std::lock_guard<std::mutex> lock(mu);
-    if (!ready[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        addr[dev] = (char *)p;
-        ready[dev] = true;
-    }
-    *out = addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = (char *)p;
     return PR_OK;
 }
 
@@ -1790,6 +1780,11 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_noalloc: ldc < n_cols");
     if (!(eps > 0.0 && eps < 1.0) || floor(1.0 / eps) > 32766.0)
         return fail(PR_ERR_INVALID, "pr_assign_noalloc: need 0 < eps < 1 and floor(1/eps) <= 32766");
+    // the same source check as pr_assign: pageable host memory is refused
+    // here, pinned host memory is read through its device mapping
+    const void *Cd = nullptr;
+    pr_status vrc = device_view(C, &Cd, "pr_assign_noalloc");
+    if (vrc != PR_OK) return vrc;
     const NoAllocLayout L = make_noalloc_layout(n_rows, n_cols);
     if (L.total > kNoAllocBytes) return fail(PR_ERR_WORKSPACE, "pr_assign_noalloc: scratch layout too large");
     PhaseCfg cfg;
@@ -1815,7 +1810,7 @@ extern "C" pr_status pr_assign_noalloc(const void *C, pr_dtype dt, int64_t ldc, 
     p.nA = n_cols;
     p.ldq = L.ldq;
     CostSource src;
-    src.C = C;
+    src.C = Cd;
     src.dt = dt;
     src.ldc = ldc;
     return launch_solve(p, src, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, false,

@@ -20,8 +20,8 @@ __device__ __forceinline__ uint32_t quantise_elem(const float *row, int a, const
     return quantise_fbits(__float_as_uint(row[a]), e);
 }
 
-// CB is the stored type: uint16_t, or uint8_t when every cbar <= 254 (the
-// caller checks floor(1/eps) <= 254); padding columns get 0x7FFF / 0xFF.
+// CB is the stored type: uint16_t, or uint8_t when every cbar <= 252 (the
+// caller checks floor(1/eps) <= 252); padding columns get 0x7FFF / 0xFF.
 template <class T, bool VEC, class CB>
 __global__ void k_quantise(const T *__restrict__ C, long long ldc, int nB, int nA, int ldq,
                            EpsSplit e, CB *__restrict__ cb, WsHead *head) {
