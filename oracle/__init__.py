@@ -36,6 +36,7 @@ MODE_SEQUENTIAL = 8
 MODE_EVICT_RESUME = 16
 MODE_OFFSET = 32
 MODE_PARALLEL = 64
+MODE_ISRAELI_ITAI = 128
 
 
 class Stats(ctypes.Structure):
@@ -109,6 +110,8 @@ def _declare(L):
     L.or_cost_f32.restype = c_dbl
     L.or_hungarian.argtypes = [_f64p, c_i64, c_i32, c_i32, _i32p]
     L.or_hungarian.restype = c_dbl
+    L.or_ii_key.argtypes = [ctypes.c_uint32] * 5
+    L.or_ii_key.restype = ctypes.c_uint64
     if hasattr(L, "or_ot_cluster_int"):
         from . import ot as _ot
         _ot._declare(L)
@@ -204,6 +207,12 @@ def assign(C: np.ndarray, eps: float, mode: int = MODE_RESUME):
     c = cost(C, r["match_b"])
     return dict(row_to_col=r["match_b"], col_to_row=r["match_a"], y_row=r["y_b"],
                 y_col=r["y_a"], cost=c, stats=r["stats"], cbar=cb, threshold=T)
+
+
+def ii_key(step: int, phase: int, it: int, u: int, v: int) -> int:
+    """Key of candidate v for vertex u in the randomized rule's step `step`
+    (see prot_oracle.c): 40 random bits above the 24-bit candidate index."""
+    return int(lib().or_ii_key(step, phase, it, u, v))
 
 
 def check_state(cb, match_b, match_a, y_b, y_a) -> int:

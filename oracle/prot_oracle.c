@@ -148,6 +148,131 @@ static uint64_t splitmix64(uint64_t x)
     return x ^ (x >> 31);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Step I by Israeli and Itai's randomized maximal matching (A. Israeli and  */
+/* A. Itai, "A fast and simple randomized parallel algorithm for maximal     */
+/* matching", IPL 22, 1986), which Sec. 3.2 names for the O(log n) parallel  */
+/* bound of a phase.  One iteration on the admissible graph of the phase's   */
+/* free rows and untaken columns:                                            */
+/*   1. every vertex with an edge points to one neighbour, chosen uniformly; */
+/*   2. every vertex pointed at keeps one of the pointers, chosen uniformly; */
+/*   3. the kept pointers leave every vertex at most two edges; it picks one */
+/*      of them, uniformly; an edge picked by both its ends joins M'.        */
+/* Matched vertices, and rows with no edge left, leave; the iterations go on */
+/* while some row has an edge, so M' ends maximal.                           */
+/*                                                                           */
+/* A uniform choice among candidates is the candidate with the least key,    */
+/* key = (draw >> 24) << 24 | candidate index: 40 random bits, then the      */
+/* index (which also settles ties); a choice between two edges in step 3     */
+/* takes the low bit of a draw.  Draws are three SplitMix64 rounds (Steele,  */
+/* Lea and Flood 2014) over (step, phase, iteration), then the vertex, then  */
+/* the other end; vertex ids are b for row b and 2^24 + a for column a.      */
+/* ------------------------------------------------------------------------ */
+#define II_COL (1u << 24)
+
+static uint64_t ii_draw(uint32_t step, uint32_t phase, uint32_t iter, uint32_t u, uint32_t v)
+{
+    uint64_t x = splitmix64(((uint64_t)step << 56) ^ ((uint64_t)phase << 28) ^ (uint64_t)iter);
+    x = splitmix64(x ^ (uint64_t)u);
+    return splitmix64(x ^ (uint64_t)v);
+}
+
+/* Key of candidate v (an index below 2^24) for vertex u. */
+uint64_t or_ii_key(uint32_t step, uint32_t phase, uint32_t iter, uint32_t u, uint32_t v)
+{
+    return ((ii_draw(step, phase, iter, u, v) >> 24) << 24) | (uint64_t)(v & 0xFFFFFFu);
+}
+
+/* One phase's step I by the randomized rule: mate[b] for b in F (-1: none),
+ * taken[a] = 1 for the columns of M'.  Returns the iterations with an edge,
+ * or -1 when OR_II_MAX_ITERS iterations did not make M' maximal. */
+static int64_t israeli_itai_phase(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *y_b,
+                                  const int32_t *y_a, const int32_t *F, int32_t nf, uint32_t phase,
+                                  int32_t *mate, int32_t *taken, int64_t *scanned)
+{
+    const uint64_t NONE = UINT64_MAX;
+    int32_t *act = (int32_t *)malloc(sizeof(int32_t) * (size_t)nB);
+    int32_t *rp = (int32_t *)malloc(sizeof(int32_t) * (size_t)nB);   /* step 1, rows    */
+    int32_t *rc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nB);   /* step 3, rows    */
+    int32_t *cc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nA);   /* step 3, columns */
+    uint64_t *cp = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nA);   /* step 1, columns */
+    uint64_t *cin = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nA);  /* step 2, columns */
+    uint64_t *rin = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nB);  /* step 2, rows    */
+    int64_t rounds = 0;
+    for (int32_t b = 0; b < nB; ++b) act[b] = 0;
+    for (int32_t i = 0; i < nf; ++i) act[F[i]] = 1;
+    for (uint32_t it = 1;; ++it) {
+        if (it > OR_II_MAX_ITERS) { rounds = -1; break; }
+        /* step 1: rows and columns point to a neighbour */
+        int32_t any = 0;
+        for (int32_t a = 0; a < nA; ++a) cp[a] = NONE;
+        for (int32_t b = 0; b < nB; ++b) {
+            rp[b] = -1;
+            if (!act[b]) continue;
+            uint64_t best = NONE;
+            for (int32_t a = 0; a < nA; ++a) {
+                *scanned += 1;
+                if (taken[a] || y_a[a] + y_b[b] != cb[(int64_t)b * nA + a] + 1) continue;
+                uint64_t kr = or_ii_key(1, phase, it, (uint32_t)b, (uint32_t)a);
+                if (kr < best) { best = kr; rp[b] = a; }
+                uint64_t kc = or_ii_key(1, phase, it, II_COL + (uint32_t)a, (uint32_t)b);
+                if (kc < cp[a]) cp[a] = kc;
+            }
+            if (rp[b] < 0) act[b] = 0;   /* no edge left: relabelled at the phase end */
+            else any = 1;
+        }
+        if (!any) break;
+        rounds += 1;
+        /* step 2: keep one incoming pointer */
+        for (int32_t a = 0; a < nA; ++a) cin[a] = NONE;
+        for (int32_t b = 0; b < nB; ++b) rin[b] = NONE;
+        for (int32_t b = 0; b < nB; ++b) {
+            if (rp[b] < 0) continue;
+            int32_t a = rp[b];
+            uint64_t k = or_ii_key(2, phase, it, II_COL + (uint32_t)a, (uint32_t)b);
+            if (k < cin[a]) cin[a] = k;
+        }
+        for (int32_t a = 0; a < nA; ++a) {
+            if (cp[a] == NONE) continue;
+            int32_t b = (int32_t)(cp[a] & 0xFFFFFFu);
+            uint64_t k = or_ii_key(2, phase, it, (uint32_t)b, (uint32_t)a);
+            if (k < rin[b]) rin[b] = k;
+        }
+        /* step 3: every vertex picks one of its remaining edges */
+        for (int32_t b = 0; b < nB; ++b) {
+            rc[b] = -1;
+            if (!act[b]) continue;
+            int32_t out = (rp[b] >= 0 && cin[rp[b]] != NONE && (int32_t)(cin[rp[b]] & 0xFFFFFFu) == b) ? rp[b] : -1;
+            int32_t in = rin[b] != NONE ? (int32_t)(rin[b] & 0xFFFFFFu) : -1;
+            if (out >= 0 && in >= 0)
+                rc[b] = (ii_draw(3, phase, it, (uint32_t)b, 0) & 1) ? in : out;
+            else
+                rc[b] = out >= 0 ? out : in;
+        }
+        for (int32_t a = 0; a < nA; ++a) {
+            cc[a] = -1;
+            if (taken[a]) continue;
+            int32_t out = -1;
+            if (cp[a] != NONE) {
+                int32_t b = (int32_t)(cp[a] & 0xFFFFFFu);
+                if (rin[b] != NONE && (int32_t)(rin[b] & 0xFFFFFFu) == a) out = b;
+            }
+            int32_t in = cin[a] != NONE ? (int32_t)(cin[a] & 0xFFFFFFu) : -1;
+            if (out >= 0 && in >= 0)
+                cc[a] = (ii_draw(3, phase, it, II_COL + (uint32_t)a, 0) & 1) ? in : out;
+            else
+                cc[a] = out >= 0 ? out : in;
+        }
+        /* edges picked at both ends join M' */
+        for (int32_t b = 0; b < nB; ++b) {
+            int32_t a = rc[b];
+            if (a >= 0 && cc[a] == b) { mate[b] = a; taken[a] = 1; act[b] = 0; }
+        }
+    }
+    free(act); free(rp); free(rc); free(cc); free(cp); free(cin); free(rin);
+    return rounds;
+}
+
 /*
  * One run of the main routine of Sec. 2.2 on integer costs cb (row-major,
  * nB x nA, nB <= nA).  Outputs the matching before completion and both dual
@@ -230,7 +355,12 @@ int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T,
             }
         }
 
-        if (mode & OR_MODE_SEQUENTIAL) {
+        if (mode & OR_MODE_ISRAELI_ITAI) {
+            int64_t r = israeli_itai_phase(cb, nB, nA, y_b, y_a, F, nf, (uint32_t)st->phases, mate, taken,
+                                           &st->scanned);
+            if (r < 0) { rc = OR_ERR_NO_CONVERGENCE; break; }
+            st->rounds += r;
+        } else if (mode & OR_MODE_SEQUENTIAL) {
             /* The paper's sequential greedy (Lemma 3.4): process B' in
              * ascending order, give each b its first admissible a that is not
              * yet matched in M'.  A different, equally valid maximal M'. */

@@ -25,6 +25,17 @@
 #define OR_MODE_EVICT_RESUME 16 /* a row evicted in phase p starts its scan in
                                    phase p+1 after the column it lost (same
                                    results; fewer entries examined)         */
+#define OR_MODE_ISRAELI_ITAI 128 /* step I by Israeli and Itai's randomized
+                                    maximal matching (Sec. 3.2, parallel
+                                    efficiency): every vertex points to a
+                                    random neighbour, keeps one random
+                                    incoming pointer, picks one of its <= 2
+                                    remaining edges; edges picked at both
+                                    ends join M'; repeat until maximal.
+                                    Random choices are minima of seeded
+                                    SplitMix64 draws (see prot_oracle.c)   */
+#define OR_II_MAX_ITERS 4096     /* iterations per phase before the oracle
+                                    reports no convergence                  */
 
 typedef struct {
     int64_t phases;       /* phases executed                                  */
@@ -40,6 +51,7 @@ int or_quantise_f64(const double *C, int64_t ldc, int32_t nB, int32_t nA, double
 int or_quantise_f32(const float *C, int64_t ldc, int32_t nB, int32_t nA, double eps, int32_t *cb);
 int32_t or_threshold(double eps, int32_t nB);
 int64_t or_phase_cap(double eps, int32_t nB);
+uint64_t or_ii_key(uint32_t step, uint32_t phase, uint32_t iter, uint32_t u, uint32_t v);
 int64_t or_check_state(const int32_t *cb, int32_t nB, int32_t nA, const int32_t *match_b,
                        const int32_t *match_a, const int32_t *y_b, const int32_t *y_a);
 int or_assign_int(const int32_t *cb, int32_t nB, int32_t nA, int32_t T, int32_t mode,

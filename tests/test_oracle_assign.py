@@ -513,3 +513,142 @@ def test_state_checker_catches_planted_mistakes():
     if free_a.size:
         assert bad(y_a=lambda v: v.__setitem__(int(free_a[0]), -1)) > 0
     assert bad(match_a=lambda v: v.__setitem__(a, -1)) > 0
+
+
+# -------------------------------------------------------------------------
+# A third step I rule: Israeli and Itai's randomized maximal matching
+# (Sec. 3.2, parallel efficiency), OR_MODE_ISRAELI_ITAI
+# -------------------------------------------------------------------------
+
+_COL = 1 << 24
+
+
+def _ii_draw(step, phase, it, u, v):
+    """Three SplitMix64 rounds: over (step, phase, iteration), then the
+    vertex id, then the other end."""
+    x = _splitmix64(((step << 56) ^ (phase << 28) ^ it) & ((1 << 64) - 1))
+    x = _splitmix64(x ^ u)
+    return _splitmix64(x ^ v)
+
+
+def _ii_key(step, phase, it, u, v):
+    return ((_ii_draw(step, phase, it, u, v) >> 24) << 24) | (v & 0xFFFFFF)
+
+
+def test_israeli_itai_key_equals_its_definition():
+    g = np.random.default_rng(5)
+    for _ in range(200):
+        args = [int(g.integers(1, 4)), int(g.integers(1, 1 << 20)), int(g.integers(1, 5000)),
+                int(g.integers(0, 1 << 25)), int(g.integers(0, 1 << 24))]
+        assert oracle.ii_key(*args) == _ii_key(*args)
+
+
+def _israeli_itai_literal(cb, T):
+    """Sec. 2.2 with step I by Israeli-Itai rounds, written out in Python.
+    Per iteration on the admissible graph of the live free rows and the
+    columns not yet in M': (1) each vertex with an edge points to the
+    neighbour of least key; (2) each vertex pointed at keeps the pointer of
+    least key; (3) each vertex picks one of its kept edges (the one it points
+    along, the one kept pointing at it; a coin bit when both), and an edge
+    picked at both ends joins M'.  Rows without an edge drop out."""
+    nB, nA = len(cb), len(cb[0])
+    yb, ya = [1] * nB, [0] * nA
+    mb, ma = [-1] * nB, [-1] * nA
+    phases = rounds = 0
+    while True:
+        F = [b for b in range(nB) if mb[b] < 0]
+        if len(F) <= T:
+            break
+        phases += 1
+        live, taken, mate = set(F), set(), {b: -1 for b in F}
+        it = 0
+        while True:
+            it += 1
+            edges = {b: [a for a in range(nA) if a not in taken and ya[a] + yb[b] == cb[b][a] + 1]
+                     for b in sorted(live)}
+            live = {b for b in live if edges[b]}
+            if not live:
+                break
+            rounds += 1
+            out_r = {b: min(edges[b], key=lambda a: _ii_key(1, phases, it, b, a)) for b in live}
+            nbr_c = {}
+            for b in live:
+                for a in edges[b]:
+                    nbr_c.setdefault(a, []).append(b)
+            out_c = {a: min(bs, key=lambda b: _ii_key(1, phases, it, _COL + a, b)) for a, bs in nbr_c.items()}
+            in_c, in_r = {}, {}
+            for b, a in out_r.items():
+                if a not in in_c or _ii_key(2, phases, it, _COL + a, b) < _ii_key(2, phases, it, _COL + a, in_c[a]):
+                    in_c[a] = b
+            for a, b in out_c.items():
+                if b not in in_r or _ii_key(2, phases, it, b, a) < _ii_key(2, phases, it, b, in_r[b]):
+                    in_r[b] = a
+
+            def pick(u, out, inn):
+                if out is not None and inn is not None:
+                    return inn if _ii_draw(3, phases, it, u, 0) & 1 else out
+                return out if out is not None else inn
+
+            pr = {b: pick(b, out_r[b] if in_c.get(out_r[b]) == b else None, in_r.get(b)) for b in live}
+            pc = {a: pick(_COL + a, out_c[a] if in_r.get(out_c[a]) == a else None, in_c.get(a))
+                  for a in nbr_c}
+            for b in sorted(live):
+                a = pr[b]
+                if a is not None and pc.get(a) == b:
+                    mate[b] = a
+                    taken.add(a)
+            live -= {b for b in live if mate[b] >= 0}
+        for b in F:
+            a = mate[b]
+            if a >= 0:
+                if ma[a] >= 0:
+                    mb[ma[a]] = -1
+                ma[a], mb[b] = b, a
+        for b in F:
+            if mate[b] >= 0:
+                ya[mate[b]] -= 1
+            else:
+                yb[b] += 1
+    return mb, ma, yb, ya, phases, rounds
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_israeli_itai_equals_literal_restatement(seed):
+    g = np.random.default_rng(100 + seed)
+    n = int(g.integers(2, 10))
+    C = rand_costs(seed, n, n + int(g.integers(0, 3)), "few" if seed % 2 else "uniform")
+    for eps in (0.5, 0.2, 0.1):
+        cb = oracle.quantise(C, eps)
+        T = oracle.threshold(eps, C.shape[0])
+        r = oracle.assign_int(cb, T, mode=oracle.MODE_ISRAELI_ITAI)
+        mb, ma, yb, ya, ph, rd = _israeli_itai_literal(cb.tolist(), T)
+        assert r["match_b"].tolist() == mb and r["match_a"].tolist() == ma
+        assert r["y_b"].tolist() == yb and r["y_a"].tolist() == ya
+        assert r["stats"]["phases"] == ph and r["stats"]["rounds"] == rd
+
+
+@pytest.mark.parametrize("n,eps,sq", [(60, 0.1, True), (150, 0.02, False), (300, 0.005, True)])
+def test_israeli_itai_invariants_and_bound(n, eps, sq):
+    """Every phase leaves a maximal M' (a relabelled row with an admissible
+    untaken column would break Eq. 2, which the per-phase check sees),
+    (I1)/(I2) and Lemma 2.1 hold, and the cost is within 3 eps n of the
+    optimum (Sec. 2.1)."""
+    C = W.assignment_sq_euclid_2d(n, 3) if sq else W.assignment_euclid_2d(n, 3)
+    r = oracle.assign(C, eps, mode=oracle.MODE_ISRAELI_ITAI | oracle.MODE_CHECK)
+    assert r["stats"]["violations"] == 0
+    opt, _ = oracle.hungarian(C)
+    assert opt - 1e-12 <= r["cost"] <= opt + 3 * eps * n + 1e-12
+
+
+def test_israeli_itai_rounds_stay_logarithmic():
+    """Where most edges are admissible (MNIST-shaped, eps = 0.75) the
+    lowest-index rule needs hundreds of rounds in its one phase; the
+    randomized rule stays within a few times log2 n (Sec. 3.2)."""
+    A, B = W.mnist_shaped_pair(400, 3)
+    C = W.l1_cost(A, B)
+    cb = oracle.quantise(C, 0.75)
+    T = oracle.threshold(0.75, 400)
+    low = oracle.assign_int(cb, T)["stats"]
+    ii = oracle.assign_int(cb, T, mode=oracle.MODE_ISRAELI_ITAI)["stats"]
+    assert ii["phases"] == 1
+    assert ii["rounds"] <= 4 * np.log2(400) < low["rounds"]
