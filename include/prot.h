@@ -124,10 +124,25 @@ pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int
  *                   Flood 2014) and stops after one full turn.  Spreading the
  *                   first proposals over the columns cuts the rounds of a
  *                   phase where most edges are admissible (large eps).
+ *   PR_RULE_ISRAELI_ITAI  Israeli and Itai's randomized maximal matching
+ *                   (IPL 1986), named by Sec. 3.2 for the O(log n) rounds of
+ *                   a phase: per round every live free row and every column
+ *                   not yet in M' points to a random admissible neighbour,
+ *                   every vertex pointed at keeps one random pointer, every
+ *                   vertex picks one of its (at most two) kept edges, and
+ *                   edges picked at both ends join M'.  Each random choice
+ *                   is the least key (draw >> 24) << 24 | index over the
+ *                   candidates, a draw being three SplitMix64 rounds over
+ *                   (step, phase, round), the vertex (b, or 2^24 + a for a
+ *                   column) and the candidate: deterministic, so the result
+ *                   is reproducible.  Every round scans each live row whole.
+ *                   Runs on the whole grid (never the cluster form); more
+ *                   than 4096 rounds in one phase return
+ *                   PR_ERR_NO_CONVERGENCE.
  * Other arguments, outputs and errors as pr_assign; cells_examined counts
  * the columns each scan passes.
  */
-typedef enum { PR_RULE_LOWEST = 0, PR_RULE_OFFSET = 1 } pr_rule;
+typedef enum { PR_RULE_LOWEST = 0, PR_RULE_OFFSET = 1, PR_RULE_ISRAELI_ITAI = 2 } pr_rule;
 pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
                          int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
                          int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,

@@ -73,8 +73,10 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
        results are copied back (the end-to-end path).
     Returns a dict: row_to_col, col_to_row (int32), y_row, y_col (int32 duals
     in units of eps), cost (float64 scalar tensor) and, when sync, stats.
-    rule: the maximal matching of step (I), "lowest" (lowest-index columns)
-    or "offset" (seeded start columns per row and phase); see pr_assign_rule.
+    rule: the maximal matching of step (I), "lowest" (lowest-index columns),
+    "offset" (seeded start columns per row and phase) or "israeli-itai"
+    (Israeli and Itai's randomized maximal matching, Sec. 3.2); see
+    pr_assign_rule.
     results_on_device: for CPU input, leave the results on the device (no
     copy back, no synchronisation when sync is False).
     """
@@ -126,8 +128,10 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
         rc = L.pr_assign(*args)
     elif rule == "offset":
         rc = L.pr_assign_rule(_lib.PR_RULE_OFFSET, *args)
+    elif rule == "israeli-itai":
+        rc = L.pr_assign_rule(_lib.PR_RULE_ISRAELI_ITAI, *args)
     else:
-        raise ValueError("rule must be 'lowest' or 'offset'")
+        raise ValueError("rule must be 'lowest', 'offset' or 'israeli-itai'")
     _lib.check(rc, "pr_assign")
     res = dict(out)
     if sync:

@@ -102,7 +102,7 @@ constexpr int kProfSegs = 7;
 __device__ __forceinline__ unsigned long long ptimer() { return (unsigned long long)clock64(); }
 
 struct Layout {
-    size_t ctl, cb, ka, prop, won, pool, lists, total;
+    size_t ctl, cb, ka, prop, won, pool, lists, ii, total;
     int ldq, won_words;
     size_t list_stride;  // ints per CTA in the list region
 };
@@ -123,6 +123,8 @@ Layout make_layout(int nB, int nA, int grid) {
     L.pool = c.take<int2>(2 * (size_t)nB);
     L.list_stride = 8 * (size_t)nB;
     L.lists = c.take<int>((size_t)grid * L.list_stride);
+    // PR_RULE_ISRAELI_ITAI's state (rule_ii.cuh): 28 bytes per column, 36 per row
+    L.ii = c.take<unsigned long long>((size_t)(2 * nA + nB) + ((size_t)(7 * nB + 3 * nA) + 1) / 2 + 64);
     L.total = c.total();
     return L;
 }
@@ -144,7 +146,8 @@ struct Params {
     int profile;
     int nslots;        // cluster mode: row slots in shared memory (one per scanning warp)
     int slot_bytes;    // bytes per row slot (a whole cbar row, 128-byte multiple)
-    int rule = 0;      // step I: 0 lowest-index columns, 1 seeded start columns (PR_RULE_OFFSET)
+    int rule = 0;      // step I: 0 lowest-index columns, 1 seeded start columns (PR_RULE_OFFSET), 2 Israeli-Itai
+    void *ii = nullptr;  // PR_RULE_ISRAELI_ITAI's state region
 };
 
 // PR_RULE_OFFSET: in phase `phase1` (counted from 1) free row b starts its
@@ -968,6 +971,8 @@ done:
     }
 }
 
+#include "rule_ii.cuh"
+
 // ---------------------------------------------------------------------------
 // k_decode: the matching is the per-column words' rows; y(A) = -k.
 // ---------------------------------------------------------------------------
@@ -1481,8 +1486,29 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
     const int kb = cb8 ? 1 : 2;  // bytes per key in the shared-memory copy
     const size_t slot_room = cfg.smem > slots_offset(p.ldq, kb) ? cfg.smem - slots_offset(p.ldq, kb) : 0;
     p.nslots = (int)std::min<size_t>((size_t)kWarps, slot_room / (size_t)p.slot_bytes);
-    const bool cluster = use_cluster(cfg, p.nslots, n_rows);
-    if (cluster) {
+    const bool cluster = p.rule != PR_RULE_ISRAELI_ITAI && use_cluster(cfg, p.nslots, n_rows);
+    if (p.rule == PR_RULE_ISRAELI_ITAI) {
+        if (!p.ii) return fail(PR_ERR_INVALID, "%s: the Israeli-Itai rule needs a workspace", who);
+        // the rule's state: 8-byte words first, then the int arrays
+        IIWork w;
+        unsigned long long *q = (unsigned long long *)p.ii;
+        w.cp = q;
+        w.cin = q + n_cols;
+        w.rin = q + 2 * (size_t)n_cols;
+        int *r = (int *)(q + 2 * (size_t)n_cols + n_rows);
+        w.mB = r;
+        w.act = r + n_rows;
+        w.mate = r + 2 * (size_t)n_rows;
+        w.rp = r + 3 * (size_t)n_rows;
+        w.rc = r + 4 * (size_t)n_rows;
+        w.mA = r + 5 * (size_t)n_rows;
+        w.taken = w.mA + n_cols;
+        w.cc = w.taken + n_cols;
+        Params pc = p;
+        void *args[] = {(void *)&pc, (void *)&w};
+        const void *fn = cb8 ? (const void *)k_ii<uint8_t> : (const void *)k_ii<uint16_t>;
+        PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, 0, st));
+    } else if (cluster) {
         cudaLaunchConfig_t c = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1623,6 +1649,7 @@ pr_status assign_common(const CostSource &src, int32_t n_rows, int32_t n_cols, d
     p.nA = n_cols;
     p.ldq = L.ldq;
     p.rule = rule;
+    p.ii = w + L.ii;
     return launch_solve(p, src, eps, cfg, row_to_col, col_to_row, y_col, cost, stats, true, who, st);
 }
 
@@ -1651,7 +1678,8 @@ extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, in
                                     int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
                                     int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
                                     size_t ws_bytes, void *stream) {
-    if (rule != PR_RULE_LOWEST && rule != PR_RULE_OFFSET) return fail(PR_ERR_INVALID, "pr_assign_rule: bad rule");
+    if (rule != PR_RULE_LOWEST && rule != PR_RULE_OFFSET && rule != PR_RULE_ISRAELI_ITAI)
+        return fail(PR_ERR_INVALID, "pr_assign_rule: bad rule");
     if (!C) return fail(PR_ERR_INVALID, "pr_assign_rule: NULL pointer argument");
     if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_rule: bad dtype");
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_rule: ldc < n_cols");

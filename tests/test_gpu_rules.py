@@ -1,7 +1,9 @@
-"""GPU parity of the seeded-start-column rule of step (I) (pr_assign_rule
-with PR_RULE_OFFSET) against the oracle's OR_MODE_OFFSET: bit-exact
+"""GPU parity of the other rules of step (I) against the oracle: the
+seeded-start-column rule (pr_assign_rule with PR_RULE_OFFSET, the oracle's
+OR_MODE_OFFSET) in every phase-loop form, and Israeli and Itai's randomized
+maximal matching (PR_RULE_ISRAELI_ITAI, OR_MODE_ISRAELI_ITAI): bit-exact
 matching, both dual vectors, phase and round counts, and the exact number of
-cost entries the scans pass, in every phase-loop form."""
+cost entries the scans pass."""
 import numpy as np
 import pytest
 
@@ -29,10 +31,10 @@ def set_form(monkeypatch, form):
     monkeypatch.setenv("PR_SCAN", "auto" if form == "grid-slots" else "regs")
 
 
-def check(prot, C, eps):
+def check(prot, C, eps, rule="offset"):
     import torch
-    r = prot.assign(torch.from_numpy(C).cuda(), eps, rule="offset")
-    ref = oracle.assign(C, eps, mode=oracle.MODE_OFFSET)
+    r = prot.assign(torch.from_numpy(C).cuda(), eps, rule=rule)
+    ref = oracle.assign(C, eps, mode=oracle.MODE_OFFSET if rule == "offset" else oracle.MODE_ISRAELI_ITAI)
     for k in ("row_to_col", "col_to_row", "y_row", "y_col"):
         assert np.array_equal(r[k].cpu().numpy(), ref[k]), k
     for k in ("phases", "rounds", "free_at_stop"):
@@ -89,3 +91,48 @@ def test_bad_rule(prot):
     rc = L.pr_assign_rule(7, C.data_ptr(), 1, 10, 10, 10, 0.1, None, None, None, None, None,
                           ctypes.byref(st), None, 0, None)
     assert rc == _lib.PR_ERR_INVALID
+
+
+# ---------------------------------------------------------------------------
+# Israeli-Itai rounds (Sec. 3.2, parallel efficiency)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,eps", [(7, 0.1), (64, 0.1), (300, 0.02), (1000, 0.01), (2049, 0.005),
+                                   (700, 0.002), (1500, 0.1)])
+def test_israeli_itai_parity(prot, n, eps):
+    """Byte and 16-bit storage (eps = 0.002), one and many phases, ragged
+    row lengths: the GPU's rounds pick the oracle's edges."""
+    check(prot, W.assignment_euclid_2d(n, 70 + n), eps, rule="israeli-itai")
+
+
+def test_israeli_itai_unbalanced_and_fp32(prot):
+    C = W.assignment_euclid_2d(400, 6, n_a=1100)
+    check(prot, C, 0.05, rule="israeli-itai")
+    check(prot, C.astype(np.float32), 0.02, rule="israeli-itai")
+
+
+@pytest.mark.parametrize("eps", [0.75, 0.5, 0.1])
+def test_israeli_itai_mnist_shaped(prot, eps):
+    """Where most edges are admissible a phase takes a few rounds, against
+    hundreds for the lowest-index rule; the Lemma 3.1 bound holds."""
+    import torch
+    A, B = W.mnist_shaped_pair(600, 5)
+    C = W.l1_cost(A, B)
+    r, _ = check(prot, C, eps, rule="israeli-itai")
+    if eps == 0.75:
+        low = prot.assign(torch.from_numpy(C).cuda(), eps)
+        assert r["stats"]["rounds"] * 10 < low["stats"]["rounds"]
+        assert r["stats"]["rounds"] <= 4 * np.log2(600)
+    opt, _ = oracle.hungarian(C)
+    assert opt - 1e-9 <= float(r["cost"]) <= opt + 3 * eps * 600 + 1e-9
+
+
+def test_israeli_itai_repeatable(prot):
+    """The draws are keyed, not taken from a device generator: two solves
+    give the same bits."""
+    import torch
+    C = torch.from_numpy(W.assignment_euclid_2d(1200, 8)).cuda()
+    a = prot.assign(C, 0.01, rule="israeli-itai")
+    b = prot.assign(C, 0.01, rule="israeli-itai")
+    for k in ("row_to_col", "y_row", "y_col"):
+        assert torch.equal(a[k], b[k])
