@@ -196,6 +196,24 @@ def ncu_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+# Dependent global round trips one round of the phase loop cannot avoid:
+# the round-start state (the last round's bitmap and proposal words), the
+# row scan's first chunk, the proposal atomic.
+ROUND_TRIPS_PER_ROUND = 3
+
+
+def latency_roofline(barriers, barrier_ns, l2_ns, kernel_ms):
+    """The phase loop against its latency floor: every round passes one grid
+    barrier and makes ROUND_TRIPS_PER_ROUND dependent L2 round trips, each
+    measured alone on this device (pr_probe_latency)."""
+    floor_ms = barriers * (barrier_ns + ROUND_TRIPS_PER_ROUND * l2_ns) * 1e-6
+    return {"bound": "latency", "floor_ms": floor_ms, "kernel_ms": kernel_ms,
+            "frac": floor_ms / kernel_ms if kernel_ms > 0 else None,
+            "barriers": int(barriers), "barrier_ns": barrier_ns, "l2_round_trip_ns": l2_ns,
+            "round_trips_per_round": ROUND_TRIPS_PER_ROUND,
+            "def": "barriers x (measured grid barrier + 3 measured dependent L2 loads) / phase-loop time"}
+
+
 def max_over_ranks(value, dist, device):
     """The largest of one float over all ranks (every rank gets it); the
     value itself without a process group."""
@@ -295,14 +313,15 @@ def run_extras(a, torch, prot, W, dev, stream):
     ws = prot.Workspace(dev)
     sweep = {}
     for eps in (0.1, 0.01, 0.005):
-        for rule in ("lowest", "offset"):
+        for rule in ("lowest", "offset", "israeli-itai"):
             if rule == "lowest" and eps == a.eps:
                 continue  # the headline line itself
             r = prot.assign(C, eps, ws=ws, rule=rule)
             out = {k: v for k, v in r.items() if k != "stats"}
             prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule)
-            ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), 10)
-            key = str(eps) if rule == "lowest" else f"{eps} offset rule"
+            reps = 10 if rule != "israeli-itai" else 3
+            ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), reps)
+            key = str(eps) if rule == "lowest" else f"{eps} {rule} rule"
             sweep[key] = {"ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
                           "cells_examined": r["stats"]["cells_examined"],
                           "bytes_scanned": r["stats"]["bytes_scanned"]}
@@ -401,12 +420,72 @@ def run_extras(a, torch, prot, W, dev, stream):
                       "speedup_vs_plain": ms_ag_plain / ms_ag}
     del costs
 
+    ex["seed_sweep"] = run_seed_sweep(a, torch, prot, W, dev, stream)
     ex["ot"] = run_ot(a, torch, prot, W, dev, reps=3)
     ex["mnist_shaped"] = run_mnist_shaped(a, torch, prot, W, dev, stream)
     ex["assign_n1000"] = run_n1000(a, torch, prot, W, dev, stream)
     if not a.no_cpu_baseline:
         ex["oracle_all_cores"] = time_oracle_parallel(a, W)
     return ex
+
+
+def device_euclid_cost(torch, A, B, dev):
+    """The workload's cost matrix formed on the device from the host points,
+    one IEEE operation at a time in the order workloads.pairwise_cost uses
+    (per coordinate: difference, square, running sum; then the square root
+    and the division by the maximum), so the bytes equal the host matrix's."""
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    acc = None
+    for d in range(A.shape[1]):
+        diff = Bt[:, d][:, None] - At[:, d][None, :]
+        sq = diff * diff
+        acc = sq if acc is None else acc + sq
+        del diff, sq
+    C = torch.sqrt(acc)
+    del acc
+    C /= C.max()
+    return C
+
+
+def run_seed_sweep(a, torch, prot, W, dev, stream, oracle_seeds=5):
+    """The headline workload over seeds 0..29: per seed the median of 5
+    timed solves on the device (costs formed on the device, bit-equal to the
+    host matrix, which is checked for seed 0), and the single-thread oracle
+    on the first `oracle_seeds` seeds (host matrices)."""
+    import statistics
+    import numpy as np
+    import oracle
+    ws = prot.Workspace(dev)
+    gpu, phases, rounds = [], [], []
+    for seed in range(30):
+        A, B = W.points_uniform(a.n, a.n, 2, seed)
+        C = device_euclid_cost(torch, A, B, dev)
+        if seed == 0:
+            same = torch.equal(C.cpu(), torch.from_numpy(W.assignment_euclid_2d(a.n, 0)))
+            if not same:
+                raise AssertionError("device cost matrix differs from the host one")
+        r = prot.assign(C, a.eps, ws=ws)
+        out = {k: v for k, v in r.items() if k != "stats"}
+        ts = [timed(torch, stream, lambda: prot.assign(C, a.eps, ws=ws, sync=False, out=out), 1) for _ in range(5)]
+        gpu.append(statistics.median(ts))
+        phases.append(r["stats"]["phases"])
+        rounds.append(r["stats"]["rounds"])
+        del C
+    cpu = []
+    if not a.no_cpu_baseline:
+        for seed in range(oracle_seeds):
+            Cn = W.assignment_euclid_2d(a.n, seed)
+            t0 = time.perf_counter()
+            oracle.assign(Cn, a.eps)
+            cpu.append(1000.0 * (time.perf_counter() - t0))
+    g = sorted(gpu)
+    return {"workload": f"assignment n={a.n} eps={a.eps}, seeds 0..29 (2-D uniform, Euclidean / max, FP64)",
+            "gpu_ms_median": statistics.median(gpu), "gpu_ms_min": g[0], "gpu_ms_max": g[-1],
+            "gpu_ms_p10": g[2], "gpu_ms_p90": g[26], "gpu_ms_per_seed": gpu,
+            "phases_median": statistics.median(phases), "rounds_median": statistics.median(rounds),
+            "phases_per_seed": phases, "rounds_per_seed": rounds,
+            "oracle_ms_1thread_median": statistics.median(cpu) if cpu else None,
+            "oracle_seeds": len(cpu)}
 
 
 def run_n1000(a, torch, prot, W, dev, stream):
@@ -468,11 +547,11 @@ def run_mnist_shaped(a, torch, prot, W, dev, stream):
     res = {"workload": f"{a.n} + {a.n} MNIST-shaped 28x28 unit-mass images (seeded strokes), "
                        "L1 cost / max"}
     for eps in (0.75, 0.5, 0.25, 0.1):
-        for rule in ("lowest", "offset"):
+        for rule in ("lowest", "offset", "israeli-itai"):
             r = prot.assign(C, eps, ws=ws, rule=rule)
             out = {k: v for k, v in r.items() if k != "stats"}
             ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), 10)
-            res[str(eps) if rule == "lowest" else f"{eps} offset rule"] = {
+            res[str(eps) if rule == "lowest" else f"{eps} {rule} rule"] = {
                 "ms": ms, "phases": r["stats"]["phases"], "rounds": r["stats"]["rounds"],
                 "cost_per_image": float(r["cost"].cpu()) / a.n}
     del C
@@ -579,6 +658,15 @@ def main():
             dist.destroy_process_group()
         return
 
+    # The measured floors under one round (outside the timed region): one grid
+    # barrier of the phase kernel's kind and one dependent L2 load.
+    wsp = torch.empty(L.pr_probe_workspace() + 256, dtype=torch.uint8, device=dev)
+    pbase = (wsp.data_ptr() + 255) & ~255
+    bar_ns, l2_ns = ctypes.c_double(), ctypes.c_double()
+    _lib.check(L.pr_probe_latency(ctypes.c_void_p(pbase), L.pr_probe_workspace(), ctypes.byref(bar_ns),
+                                  ctypes.byref(l2_ns), ctypes.c_void_p(stream.cuda_stream)), "pr_probe_latency")
+    del wsp
+
     extras = None
     if not a.no_extras and world == 1:
         extras = run_extras(a, torch, prot, W, dev, stream)
@@ -608,16 +696,24 @@ def main():
                      "bytes_per_launch": bytes_per_launch,
                      "bytes_per_launch_def": "rounded costs examined by the proposal scans x bytes per cost",
                      "bytes_loaded_per_launch": float(st["bytes_scanned"]), "peak_source": peak_src},
+        "latency_roofline": latency_roofline(st["barriers"], bar_ns.value, l2_ns.value, k_avg),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_SOLVE * a.steps,
         "clocks": clk,
-        "solver": {"phases": st["phases"], "rounds": st["rounds"], "rows_scanned": st["rows_scanned"],
+        "solver": {"phases": st["phases"], "rounds": st["rounds"], "barriers": st["barriers"],
+                   "rows_scanned": st["rows_scanned"],
                    "cells_examined": st["cells_examined"],
                    "free_at_stop": st["free_at_stop"], "threshold": st["threshold"],
                    "cost": float(ref["cost"].cpu()), "phase_loop_ms": k_avg},
         "extras": extras,
     }
+    if extras and extras.get("seed_sweep"):
+        sw = extras["seed_sweep"]
+        line["config"]["value_seed"] = a.seed
+        line["config"]["seeds_0_29_gpu_ms_median"] = sw["gpu_ms_median"]
+        line["config"]["seeds_0_29_note"] = ("value times seed 0 over the timed steps; the median over seeds "
+                                             "0..29 (5 solves each) is seeds_0_29_gpu_ms_median")
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -65,6 +65,10 @@ typedef struct {
                                examine, from each scan's start column to the
                                column it proposes to (inclusive) or to the
                                row's end; 0 for the other entry points       */
+    int64_t barriers;      /* pr_assign: grid (or cluster) barriers the phase
+                              loop passed -- one per round of the lowest-index
+                              and offset rules, rounds without a proposal
+                              included; 0 for the other entry points        */
 } pr_stats;
 
 /*
@@ -412,6 +416,21 @@ pr_status pr_ws_status(const void *ws, void *stream);
  * CUDA events.  Pass NULL, NULL to stop.  The events are borrowed, not owned.
  */
 void pr_set_kernel_events(void *start, void *stop);
+
+/*
+ * pr_probe_latency -- the measured floors under one round of the phase loop
+ * on the current device: *barrier_ns, the mean time of one grid barrier of
+ * the kind the phase kernel uses (one CTA of 512 threads per SM, a release
+ * reduction and acquire polls, 2000 in a row), and *l2_ns, the mean time of
+ * one dependent load that hits L2 (a chain of 4096 loads through a 4 MB
+ * permutation).  Diagnostics for a latency roofline; the paper has no
+ * counterpart.  `ws` is device memory of at least pr_probe_workspace()
+ * bytes, 256-byte aligned, owned by the caller.  Synchronises `stream`.
+ * Errors: PR_ERR_WORKSPACE, PR_ERR_CUDA, PR_ERR_TIMEOUT (a barrier wait ran
+ * out).
+ */
+size_t pr_probe_workspace(void);
+pr_status pr_probe_latency(void *ws, size_t ws_bytes, double *barrier_ns, double *l2_ns, void *stream);
 
 /* Thread-local text of the last error (never NULL). */
 const char *pr_last_error(void);

@@ -35,6 +35,7 @@ class PrStats(ctypes.Structure):
         ("loop_ctas", ctypes.c_int32),
         ("loop_cluster", ctypes.c_int32),
         ("cells_examined", ctypes.c_int64),
+        ("barriers", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -71,6 +72,8 @@ _sz = ctypes.c_size_t
 # name -> (restype, argtypes); every symbol include/prot.h declares.
 SIGNATURES = {
     "pr_assign_workspace": (_sz, [_i32, _i32]),
+    "pr_probe_workspace": (_sz, []),
+    "pr_probe_latency": (ctypes.c_int, [_vp, _sz, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp]),
     "pr_assign": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp,
                                  ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_assign_batched_workspace": (_sz, [_i32, _vp]),

@@ -85,6 +85,7 @@ struct Ctl {
     unsigned long long cells;  // cost entries the scans examine (start .. answer, or .. row end)
     unsigned maxbits;          // points source: bits of the largest distance (FP32, >= 0)
     int pad1;
+    unsigned long long barriers;  // barriers the phase loop passed
     // PR_PROFILE=1: a split of every round (SM clock cycles) into kProfSegs
     // segments: round start (bitmaps, keys), item build, row scans,
     // proposals, donations and the rest, grid barrier; then the item count.
@@ -957,6 +958,7 @@ done:
         if (cta == 0) {
             ctl->phases = phase;
             ctl->rounds = rounds;
+            ctl->barriers = gen;
         }
     }
     // A copy whose wait gave up gets one more bounded wait: the CTA must not
@@ -1563,6 +1565,7 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
         stats->threshold = p.T;
         stats->loop_ctas = cluster ? cfg.cluster : cfg.grid;
         stats->loop_cluster = cluster ? 1 : 0;
+        stats->barriers = (int64_t)h.barriers;
         if (h.head.err != 0)
             return fail((pr_status)h.head.err, "%s: device reported %s", who,
                         pr_status_string((pr_status)h.head.err));

@@ -731,6 +731,7 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
         stats->loop_ctas = 0;
         stats->loop_cluster = 0;
         stats->cells_examined = 0;
+        stats->barriers = 0;
         if (h.head.err != 0)
             return fail((pr_status)h.head.err, "batched: device reported %s", pr_status_string((pr_status)h.head.err));
     }

@@ -1104,6 +1104,7 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         stats->loop_ctas = 0;
         stats->loop_cluster = 0;
         stats->cells_examined = 0;
+        stats->barriers = 0;
     }
     if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
     return PR_OK;

@@ -296,5 +296,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ii(Params p, IIWork w) {
     if (t0 == 0) {
         ctl->phases = phase;
         ctl->rounds = rounds;
+        ctl->barriers = gen;
     }
 }

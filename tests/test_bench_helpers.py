@@ -44,3 +44,13 @@ def test_traffic_summary_only_for_unchanged_sources(monkeypatch):
     assert b.ncu_traffic() == d["dram_bytes_per_launch"]
     monkeypatch.setattr(b, "src_hash", lambda: "0" * 16)
     assert b.ncu_traffic() is None
+
+
+def test_latency_roofline_arithmetic():
+    """Floor = barriers x (one barrier + three dependent L2 loads); the
+    fraction is the floor over the measured phase-loop time."""
+    import bench
+    r = bench.latency_roofline(1000, 900.0, 150.0, 2.7)
+    assert abs(r["floor_ms"] - 1000 * (900.0 + 3 * 150.0) * 1e-6) < 1e-12
+    assert abs(r["frac"] - r["floor_ms"] / 2.7) < 1e-12
+    assert r["bound"] == "latency" and r["barriers"] == 1000
