@@ -14,13 +14,20 @@ constexpr uint16_t kPadCost = 0x7FFF;  // cbar of padding columns
 constexpr uint16_t kPadKey = 0x8000;   // k of padding columns: pad sum 0xFFFF never matches
 
 // eps split exactly as me * 2^ee (me < 2^53, an integer), plus the FP32
-// reciprocal used for the estimate.  Built on the host by make_eps_split.
+// reciprocal used for the estimate and the estimate's margin.  Built on the
+// host by make_eps_split.
 struct EpsSplit {
     unsigned long long me;
     int ee;
     float inv;
+    float win;  // an estimate within win of an integer takes the exact test
 };
 
+// The FP32 estimate q of c / eps (c truncated to 24 significant bits:
+// relative error < 2^-23; RN32(1/eps) and the rounded product: 2^-24 each)
+// is within c / eps * 2^-22 (1 + 2^-24) < (floor(1/eps) + 1) * 2^-22 of the
+// exact quotient, as c <= 1.  The margin is twice that, at most 1/64: at
+// eps = 0.01 it is 5e-5, so about one cost in 10^4 takes the exact test.
 inline EpsSplit make_eps_split(double eps) {  // eps normal, in (0, 1)
     unsigned long long bits;
     memcpy(&bits, &eps, sizeof bits);
@@ -28,6 +35,8 @@ inline EpsSplit make_eps_split(double eps) {  // eps normal, in (0, 1)
     e.me = (bits & ((1ull << 52) - 1)) | (1ull << 52);
     e.ee = (int)((bits >> 52) & 0x7FF) - 1075;
     e.inv = (float)(1.0 / eps);
+    const double w = (floor(1.0 / eps) + 1.0) * ldexp(1.0, -21);
+    e.win = (float)(w < 0.015625 ? w : 0.015625);
     return e;
 }
 
@@ -47,18 +56,18 @@ __device__ __forceinline__ bool ge_multiple(unsigned long long mc, int ec, uint3
 }
 
 // Eq. (1) exactly: cbar = the largest k with k * eps <= c, for 0 <= c <= 1.
-// An FP32 estimate q of c/eps is within 0.008 of the exact quotient (see
-// below), so floor(q) is exact whenever q is at least 1/64 away from an
-// integer.  Otherwise the exact quotient lies within 0.03 of the integer m
-// nearest q, so the floor is m or m - 1, settled by the exact integer test
-// c >= m * eps.  No floating-point division and no FP64 instruction runs
-// (GB300 runs FP64 at a small fraction of its FP32 rate).
+// An FP32 estimate q of c/eps is within (floor(1/eps) + 1) * 2^-22 of the
+// exact quotient (see make_eps_split), so floor(q) is exact whenever q is at
+// least e.win (twice that bound, at most 1/64) away from an integer.
+// Otherwise the exact quotient lies within 1/32 of the integer m nearest q,
+// so the floor is m or m - 1, settled by the exact integer test c >= m * eps.
+// No floating-point division and no FP64 instruction runs (GB300 runs FP64
+// at a small fraction of its FP32 rate).
 //
 // For an FP64 cost given by its bit pattern.  Range test on the bits:
 // 0 <= c <= 1 (or -0.0), which also rejects NaN and infinities.  The FP32
 // estimate truncates the mantissa (relative error < 2^-23) before the two
-// roundings of the product, so q is within 0.008 of the exact quotient
-// (which is below 2^15) and the 1/64 margin holds.
+// roundings of the product.
 // Returns 0xFFFFFFFF for a cost outside [0, 1].
 __device__ __forceinline__ uint32_t quantise_bits(uint32_t hi, uint32_t lo, const EpsSplit &e) {
     if (hi >= 0x80000000u) {  // sign bit: only -0.0 is valid
@@ -76,7 +85,7 @@ __device__ __forceinline__ uint32_t quantise_bits(uint32_t hi, uint32_t lo, cons
     const float kf = floorf(q);
     const float fr = q - kf;
     uint32_t k = (uint32_t)kf;
-    if (!(fr >= 0.015625f && fr <= 0.984375f)) {
+    if (!(fr >= e.win && fr <= 1.0f - e.win)) {
         const uint32_t m = k + (fr > 0.5f ? 1u : 0u);
         if (m == 0u) return 0u;
         const unsigned long long mc = (((unsigned long long)(hi & 0xFFFFFu) << 32) | lo) | (1ull << 52);
@@ -96,7 +105,7 @@ __device__ __forceinline__ uint32_t quantise_fbits(uint32_t fb, const EpsSplit &
     const float kf = floorf(q);
     const float fr = q - kf;
     uint32_t k = (uint32_t)kf;
-    if (!(fr >= 0.015625f && fr <= 0.984375f)) {
+    if (!(fr >= e.win && fr <= 1.0f - e.win)) {
         const uint32_t m = k + (fr > 0.5f ? 1u : 0u);
         if (m == 0u) return 0u;
         const unsigned long long mc = (unsigned long long)((fb & 0x7FFFFFu) | 0x800000u);
