@@ -180,6 +180,22 @@ pr_status pr_assign_staged(const void *C_host, void *C_dev, pr_dtype dt, int64_t
                            size_t ws_bytes, void *stream);
 
 /*
+ * pr_assign_within -- a matching whose cost is within delta * n_rows of the
+ * optimum, for costs in [0, 1].  The main routine of Sec. 2.2 with
+ * parameter eps returns a matching within 3 * eps * n_rows of the optimum
+ * (Sec. 2.1, Lemma 3.1); the paper's introduction (Sec. 1) gets the
+ * eps * n guarantee by running it with eps / 3.  This call does that: it is
+ * pr_assign with eps = delta / 3 (one IEEE FP64 division), and the duals it
+ * returns are in units of that eps.
+ *   delta  0 < delta < 3, with floor(3 / delta) <= 32766
+ * Other arguments, outputs and errors as pr_assign.
+ */
+pr_status pr_assign_within(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int32_t n_cols,
+                           double delta, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                           int32_t *y_col, double *cost, pr_stats *stats, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/*
  * pr_dual_bound -- the a-posteriori certificate of a pr_assign solve
  * (Lemma 3.1).  The duals it returns satisfy Eq. (2), y(a) + y(b) <= cbar +
  * eps on every edge; summed over any matching that covers the rows (column

@@ -62,7 +62,7 @@ def _stream_handle(torch, device):
 
 
 def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out=None,
-           rule: str = "lowest", results_on_device: bool = False):
+           rule: str = "lowest", results_on_device: bool = False, _within: bool = False):
     """Additive eps-approximate assignment (Sec. 2.2 of the paper).
 
     C: (n_rows, n_cols) float32/float64 tensor with costs in [0, 1],
@@ -122,7 +122,9 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
             out["y_row"].data_ptr(), out["y_col"].data_ptr(), out["cost"].data_ptr(),
             ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
             _stream_handle(torch, dev))
-    if staged:
+    if _within:  # eps holds delta: pr_assign_within runs the solve with delta / 3
+        rc = L.pr_assign_within(*args)
+    elif staged:
         rc = L.pr_assign_staged(C.data_ptr(), *args)
     elif rule == "lowest":
         rc = L.pr_assign(*args)
@@ -209,13 +211,20 @@ def dual_bound(result, eps: float):
 
 def assign_within(C, delta: float, **kw):
     """A matching whose cost is within delta * n_rows of the optimum (costs
-    in [0, 1]).  The main routine with parameter eps is a 3 eps
-    approximation (Sec. 2.1, Lemma 3.1); the paper's introduction obtains an
-    eps approximation by running it with eps / 3, as this does with delta.
-    Keyword arguments go to `assign`."""
+    in [0, 1]), through pr_assign_within: the main routine with parameter
+    eps is a 3 eps approximation (Sec. 2.1, Lemma 3.1), and the library runs
+    it with eps = delta / 3 as the paper's introduction does.  The duals are
+    in units of that eps.  A CPU tensor is copied to the current device
+    first.  Keyword arguments go to `assign` (the lowest-index rule)."""
+    torch = _torch()
     if not (0.0 < delta < 3.0):
         raise ValueError("need 0 < delta < 3")
-    return assign(C, delta / 3.0, **kw)
+    if kw.get("rule", "lowest") != "lowest":
+        raise ValueError("assign_within runs the lowest-index rule")
+    kw.pop("rule", None)
+    if not C.is_cuda:
+        C = C.to(torch.device("cuda", torch.cuda.current_device()))
+    return assign(C, delta, _within=True, **kw)
 
 
 def _tune_cache_path():

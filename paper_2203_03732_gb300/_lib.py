@@ -72,6 +72,8 @@ _sz = ctypes.c_size_t
 # name -> (restype, argtypes); every symbol include/prot.h declares.
 SIGNATURES = {
     "pr_assign_workspace": (_sz, [_i32, _i32]),
+    "pr_assign_within": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp,
+                                        ctypes.POINTER(PrStats), _vp, _sz, _vp]),
     "pr_probe_workspace": (_sz, []),
     "pr_probe_latency": (ctypes.c_int, [_vp, _sz, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _vp]),
     "pr_assign": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _i32, _i32, _dbl, _vp, _vp, _vp, _vp, _vp,

@@ -1677,6 +1677,16 @@ extern "C" pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t 
                          ws_bytes, stream, "pr_assign");
 }
 
+extern "C" pr_status pr_assign_within(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int32_t n_cols,
+                                      double delta, int32_t *row_to_col, int32_t *col_to_row, int32_t *y_row,
+                                      int32_t *y_col, double *cost, pr_stats *stats, void *ws, size_t ws_bytes,
+                                      void *stream) {
+    // Sec. 1: the 3 eps n routine run with eps = delta / 3 is a delta n approximation
+    if (!(delta > 0.0 && delta < 3.0)) return fail(PR_ERR_INVALID, "pr_assign_within: need 0 < delta < 3");
+    return pr_assign(C, dt, ldc, n_rows, n_cols, delta / 3.0, row_to_col, col_to_row, y_row, y_col, cost, stats,
+                     ws, ws_bytes, stream);
+}
+
 extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
                                     int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
                                     int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,

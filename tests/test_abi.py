@@ -164,3 +164,15 @@ def test_no_oracle_import_in_product_path():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "prot_oracle" not in txt, f
+
+
+def test_assign_within_refuses_delta_without_gpu(libpath):
+    """pr_assign_within checks delta (0 < delta < 3) before anything else."""
+    from paper_2203_03732_gb300 import _lib
+    L = _lib.load(libpath)
+    st = _lib.PrStats()
+    for delta in (0.0, -1.0, 3.0, float("nan")):
+        rc = L.pr_assign_within(None, 1, 10, 10, 10, delta, None, None, None, None, None,
+                                ctypes.byref(st), None, 0, None)
+        assert rc == _lib.PR_ERR_INVALID
+        assert b"delta" in L.pr_last_error()
