@@ -292,7 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ii(Params p, IIWork w) {
         for (long long a = t0; a < p.nA; a += nth)
             p.prop[a] = w.mA[a] >= 0 ? word_of(1, w.mA[a]) : word_of(0, -1);
     const unsigned long long cb = block_sum(cells, &bsum);
-    if (threadIdx.x == 0 && cb) atomicAdd(&ctl->cells, cb);
+    if (threadIdx.x == 0 && cb) {
+        atomicAdd(&ctl->cells, cb);
+        atomicAdd(&ctl->bytes, cb * sizeof(CB));  // every live row is read whole each round
+    }
     if (t0 == 0) {
         ctl->phases = phase;
         ctl->rounds = rounds;
