@@ -46,6 +46,20 @@ def assert_ot_parity(r, dense, ref):
     assert np.array_equal(dense, ref["mass"])
     c = float(r["cost"].cpu())
     assert abs(c - ref["cost"]) <= 1e-12 * abs(ref["cost"])
+    assert_free_copies_feasible(r, ref["cbar"])
+
+
+def assert_free_copies_feasible(r, cb, rows=512):
+    """Eq. 2 between each supply's returned dual F_b (its free copies' dual)
+    and the highest dual among each demand's copies: F_b + y(a) <= cbar + 1
+    in units of eps, from the GPU's own outputs."""
+    F = r["y_sup"].cpu().numpy().astype(np.int64)
+    kmin = r["dem_kmin"].cpu().numpy().astype(np.int64)
+    lo = r["dem_lo"].cpu().numpy()
+    top = np.where(lo > 0, -kmin, -kmin - 1)
+    for b0 in range(0, F.size, rows):
+        blk = cb[b0:b0 + rows].astype(np.int64)
+        assert not (F[b0:b0 + rows, None] + top[None, :] > blk + 1).any()
 
 
 @pytest.mark.parametrize("nB,nA,eps", [(20, 25, 0.1), (64, 64, 0.05), (300, 257, 0.05),

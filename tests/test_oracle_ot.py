@@ -94,6 +94,23 @@ def test_invariants_plan_and_bound(seed, eps):
     assert opt - 1e-9 <= r["cost"] <= opt + 3.5 * eps
 
 
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("eps", [0.1, 0.02])
+def test_returned_duals_are_feasible(seed, eps):
+    """What the OT form returns as duals (F_b per supply, kmin and the two
+    cluster counts per demand) satisfies Eq. 2 on its own: every supply's
+    dual F_b plus the highest dual among a demand's copies is at most
+    cbar + 1 (units of eps), including supplies with no free copy left."""
+    C, nu, mu = W.ot_euclid_2d(90 + 13 * seed, 70 + 29 * seed, 300 + seed)
+    r = O.ot(C, nu, mu, eps)
+    F = r["F"].astype(np.int64)
+    kmin = r["kmin"].astype(np.int64)
+    top = np.where(r["clo"] > 0, -kmin, -kmin - 1)
+    assert not (F[:, None] + top[None, :] > r["cbar"].astype(np.int64) + 1).any()
+    # the copy with the top dual of a demand with copies exists
+    assert ((r["clo"] + r["chi"]) > 0).any()
+
+
 def test_theta_and_counts_by_hand():
     # n = 3, eps = 0.5: theta = 24; supplies 0.5/0.25/0.25 -> 12/6/6 copies,
     # demands 1/3 each -> ceil(24/3) = 8 copies.
