@@ -313,7 +313,7 @@ def run_extras(a, torch, prot, W, dev, stream):
     ws = prot.Workspace(dev)
     sweep = {}
     for eps in (0.1, 0.01, 0.005):
-        for rule in ("lowest", "offset", "israeli-itai"):
+        for rule in ("lowest", "offset", "israeli-itai", "sequential"):
             if rule == "lowest" and eps == a.eps:
                 continue  # the headline line itself
             r = prot.assign(C, eps, ws=ws, rule=rule)
@@ -547,7 +547,7 @@ def run_mnist_shaped(a, torch, prot, W, dev, stream):
     res = {"workload": f"{a.n} + {a.n} MNIST-shaped 28x28 unit-mass images (seeded strokes), "
                        "L1 cost / max"}
     for eps in (0.75, 0.5, 0.25, 0.1):
-        for rule in ("lowest", "offset", "israeli-itai"):
+        for rule in ("lowest", "offset", "israeli-itai", "sequential"):
             r = prot.assign(C, eps, ws=ws, rule=rule)
             out = {k: v for k, v in r.items() if k != "stats"}
             ms = timed(torch, stream, lambda: prot.assign(C, eps, ws=ws, sync=False, out=out, rule=rule), 10)

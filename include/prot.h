@@ -143,10 +143,26 @@ pr_status pr_assign(const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows, int
  *                   Runs on the whole grid (never the cluster form); more
  *                   than 4096 rounds in one phase return
  *                   PR_ERR_NO_CONVERGENCE.
+ *   PR_RULE_SEQUENTIAL  the sequential greedy of Sec. 3.2 (the free rows in
+ *                   index order, each taking its first admissible column
+ *                   not yet in M'), computed without rounds: every free row
+ *                   scans on its own, a column goes to the lowest row that
+ *                   reaches it in the phase, and a row that loses a column
+ *                   to a lower one scans on after it.  The result does not
+ *                   depend on the order the scans run in; one grid barrier
+ *                   per phase.  stats->rounds counts one round per phase.
+ *                   The phase's keys are kept in shared memory, so n_cols
+ *                   is at most 196,608 with byte storage (floor(1/eps) <=
+ *                   252) and 98,304 otherwise (PR_ERR_INVALID beyond).
  * Other arguments, outputs and errors as pr_assign; cells_examined counts
  * the columns each scan passes.
  */
-typedef enum { PR_RULE_LOWEST = 0, PR_RULE_OFFSET = 1, PR_RULE_ISRAELI_ITAI = 2 } pr_rule;
+typedef enum {
+    PR_RULE_LOWEST = 0,
+    PR_RULE_OFFSET = 1,
+    PR_RULE_ISRAELI_ITAI = 2,
+    PR_RULE_SEQUENTIAL = 3
+} pr_rule;
 pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, int64_t ldc, int32_t n_rows,
                          int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
                          int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,

@@ -69,14 +69,15 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
        n_rows <= n_cols.  A CUDA tensor is solved in place on its device; a
        CPU tensor (pinned memory for asynchronous copies) is copied to the
        current CUDA device in row chunks, each chunk rounded while the next
-       is copied (pr_assign_staged; rule "offset" copies first), and the
+       is copied (pr_assign_staged; the other rules copy first), and the
        results are copied back (the end-to-end path).
     Returns a dict: row_to_col, col_to_row (int32), y_row, y_col (int32 duals
     in units of eps), cost (float64 scalar tensor) and, when sync, stats.
     rule: the maximal matching of step (I), "lowest" (lowest-index columns),
-    "offset" (seeded start columns per row and phase) or "israeli-itai"
-    (Israeli and Itai's randomized maximal matching, Sec. 3.2); see
-    pr_assign_rule.
+    "offset" (seeded start columns per row and phase), "israeli-itai"
+    (Israeli and Itai's randomized maximal matching, Sec. 3.2) or
+    "sequential" (the sequential greedy of Sec. 3.2, computed without
+    rounds); see pr_assign_rule.
     results_on_device: for CPU input, leave the results on the device (no
     copy back, no synchronisation when sync is False).
     """
@@ -132,8 +133,10 @@ def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out
         rc = L.pr_assign_rule(_lib.PR_RULE_OFFSET, *args)
     elif rule == "israeli-itai":
         rc = L.pr_assign_rule(_lib.PR_RULE_ISRAELI_ITAI, *args)
+    elif rule == "sequential":
+        rc = L.pr_assign_rule(_lib.PR_RULE_SEQUENTIAL, *args)
     else:
-        raise ValueError("rule must be 'lowest', 'offset' or 'israeli-itai'")
+        raise ValueError("rule must be 'lowest', 'offset', 'israeli-itai' or 'sequential'")
     _lib.check(rc, "pr_assign")
     res = dict(out)
     if sync:

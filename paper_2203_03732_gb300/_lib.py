@@ -49,6 +49,7 @@ class PrBatchedTune(ctypes.Structure):
 PR_RULE_LOWEST = 0
 PR_RULE_OFFSET = 1
 PR_RULE_ISRAELI_ITAI = 2
+PR_RULE_SEQUENTIAL = 3
 
 PR_SQEUCLIDEAN = 0
 PR_EUCLIDEAN = 1

@@ -95,6 +95,7 @@ struct Ctl {
     unsigned long long prof_max[8];
     unsigned long long prof_slot[2][8];  // per round parity: max over CTAs
     unsigned long long prof_rounds;
+    unsigned long long seq_tail;  // PR_RULE_SEQUENTIAL: rows queued so far (rule_seq.cuh)
 };
 constexpr int kProfSegs = 7;
 
@@ -147,7 +148,8 @@ struct Params {
     int profile;
     int nslots;        // cluster mode: row slots in shared memory (one per scanning warp)
     int slot_bytes;    // bytes per row slot (a whole cbar row, 128-byte multiple)
-    int rule = 0;      // step I: 0 lowest-index columns, 1 seeded start columns (PR_RULE_OFFSET), 2 Israeli-Itai
+    int rule = 0;      // step I: 0 lowest-index columns, 1 seeded start columns (PR_RULE_OFFSET),
+                       // 2 Israeli-Itai, 3 the sequential greedy by displacement chains
     void *ii = nullptr;  // PR_RULE_ISRAELI_ITAI's state region
 };
 
@@ -974,6 +976,7 @@ done:
 }
 
 #include "rule_ii.cuh"
+#include "rule_seq.cuh"
 
 // ---------------------------------------------------------------------------
 // k_decode: the matching is the per-column words' rows; y(A) = -k.
@@ -1488,8 +1491,17 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
     const int kb = cb8 ? 1 : 2;  // bytes per key in the shared-memory copy
     const size_t slot_room = cfg.smem > slots_offset(p.ldq, kb) ? cfg.smem - slots_offset(p.ldq, kb) : 0;
     p.nslots = (int)std::min<size_t>((size_t)kWarps, slot_room / (size_t)p.slot_bytes);
-    const bool cluster = p.rule != PR_RULE_ISRAELI_ITAI && use_cluster(cfg, p.nslots, n_rows);
-    if (p.rule == PR_RULE_ISRAELI_ITAI) {
+    const bool cluster = p.rule <= PR_RULE_OFFSET && use_cluster(cfg, p.nslots, n_rows);
+    if (p.rule == PR_RULE_SEQUENTIAL) {
+        // the phase's keys live in shared memory, one per column (the size
+        // was checked by pr_assign_rule)
+        const size_t ksm = (size_t)p.ldq * (cb8 ? 1 : 2);
+        const void *fn = cb8 ? (const void *)k_seq<uint8_t> : (const void *)k_seq<uint16_t>;
+        PR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm));
+        Params pc = p;
+        void *args[] = {(void *)&pc};
+        PR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(kThreads), args, ksm, st));
+    } else if (p.rule == PR_RULE_ISRAELI_ITAI) {
         if (!p.ii) return fail(PR_ERR_INVALID, "%s: the Israeli-Itai rule needs a workspace", who);
         // the rule's state: 8-byte words first, then the int arrays
         IIWork w;
@@ -1691,10 +1703,19 @@ extern "C" pr_status pr_assign_rule(pr_rule rule, const void *C, pr_dtype dt, in
                                     int32_t n_cols, double eps, int32_t *row_to_col, int32_t *col_to_row,
                                     int32_t *y_row, int32_t *y_col, double *cost, pr_stats *stats, void *ws,
                                     size_t ws_bytes, void *stream) {
-    if (rule != PR_RULE_LOWEST && rule != PR_RULE_OFFSET && rule != PR_RULE_ISRAELI_ITAI)
+    if (rule != PR_RULE_LOWEST && rule != PR_RULE_OFFSET && rule != PR_RULE_ISRAELI_ITAI &&
+        rule != PR_RULE_SEQUENTIAL)
         return fail(PR_ERR_INVALID, "pr_assign_rule: bad rule");
     if (!C) return fail(PR_ERR_INVALID, "pr_assign_rule: NULL pointer argument");
     if (dt != PR_F32 && dt != PR_F64) return fail(PR_ERR_INVALID, "pr_assign_rule: bad dtype");
+    if (rule == PR_RULE_SEQUENTIAL && eps > 0.0 && eps < 1.0) {
+        // the phase's keys live in shared memory, one byte (floor(1/eps) <=
+        // 252) or two per column
+        const size_t kb = (long long)floor(1.0 / eps) <= kMaxCbar8 ? 1 : 2;
+        if ((((size_t)n_cols + 15) & ~(size_t)15) * kb > kSeqMaxKeyBytes)
+            return fail(PR_ERR_INVALID, "pr_assign_rule: the sequential rule takes at most %zu columns at this eps",
+                        kSeqMaxKeyBytes / kb);
+    }
     if (ldc < n_cols) return fail(PR_ERR_INVALID, "pr_assign_rule: ldc < n_cols");
     CostSource src;
     if (row_to_col && col_to_row && y_row && y_col && cost) {  // NULL outputs: reported below

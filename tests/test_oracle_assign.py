@@ -652,3 +652,92 @@ def test_israeli_itai_rounds_stay_logarithmic():
     ii = oracle.assign_int(cb, T, mode=oracle.MODE_ISRAELI_ITAI)["stats"]
     assert ii["phases"] == 1
     assert ii["rounds"] <= 4 * np.log2(400) < low["rounds"]
+
+
+# -------------------------------------------------------------------------
+# Step I without rounds: displacement chains give the sequential greedy
+# -------------------------------------------------------------------------
+
+def _displacement_run(cb, T, rng):
+    """Sec. 2.2 with step I run as concurrent chains and no rounds: every
+    free row scans its columns in order for an admissible one; a column is
+    held by the lowest row that reached it in this phase, so a row passes a
+    column held by a lower row and takes one held by a higher row, whose row
+    then goes on scanning after that column.  The chains advance one column
+    at a time in the order `rng` draws.  A row evicted from M starts its next
+    scan after the column it lost, as in the evict-resume rule.  Steps II and
+    III are those of Sec. 2.2."""
+    nB, nA = cb.shape
+    y_b, k = [1] * nB, [0] * nA
+    partner, match_b, start = [-1] * nA, [-1] * nB, [0] * nB
+    phases = 0
+    while True:
+        free = [b for b in range(nB) if match_b[b] < 0]
+        if len(free) <= T:
+            break
+        phases += 1
+        held = {}
+        active = [(b, start[b]) for b in free]
+        for b in free:
+            start[b] = 0
+        while active:
+            i = int(rng.integers(len(active)))
+            b, a = active[i]
+            if a >= nA:
+                active.pop(i)
+                continue
+            if cb[b, a] + k[a] == y_b[b] - 1 and held.get(a, nB) > b:
+                h = held.get(a)
+                held[a] = b
+                if h is None:
+                    active.pop(i)
+                else:
+                    active[i] = (h, a + 1)
+                continue
+            active[i] = (b, a + 1)
+        mate = {b: a for a, b in held.items()}
+        for a, b in held.items():
+            old = partner[a]
+            if old >= 0:
+                match_b[old] = -1
+                start[old] = a + 1
+            partner[a], match_b[b] = b, a
+            k[a] += 1
+        for b in free:
+            if b not in mate:
+                y_b[b] += 1
+    return np.array(match_b), np.array(y_b), -np.array(k), phases
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_displacement_chains_give_the_sequential_greedy(seed):
+    """Whatever order the chains advance in, each phase ends with the
+    matching M' of the paper's sequential greedy (Sec. 3.2: rows in index
+    order, each takes its first admissible column not yet in M'), so the
+    whole run equals OR_MODE_SEQUENTIAL: matching, both duals and phases.
+    Few distinct costs make many rows compete for the same columns."""
+    g = np.random.default_rng(seed)
+    nB = int(g.integers(6, 30))
+    nA = nB + int(g.integers(0, 6))
+    eps = (0.1, 0.25, 0.05)[seed % 3]
+    C = rand_costs(seed, nB, nA, "few" if seed % 2 else "uniform")
+    cb = oracle.quantise(C, eps)
+    T = oracle.threshold(eps, nB)
+    ref = oracle.assign_int(cb, T, mode=oracle.MODE_SEQUENTIAL)
+    for order in range(3):
+        mb, yb, ya, phases = _displacement_run(cb, T, np.random.default_rng(100 * seed + order))
+        assert np.array_equal(mb, ref["match_b"])
+        assert np.array_equal(yb, ref["y_b"])
+        assert np.array_equal(ya, ref["y_a"])
+        assert phases == ref["stats"]["phases"] == ref["stats"]["rounds"]
+
+
+def test_displacement_chains_differ_from_the_round_rule():
+    """The chains are not the lowest-index round rule: on the MNIST-shaped
+    costs at eps = 0.75 the two rules pick different matchings."""
+    A, B = W.mnist_shaped_pair(60, 2)
+    C = W.l1_cost(A, B)
+    cb = oracle.quantise(C, 0.75)
+    T = oracle.threshold(0.75, 60)
+    mb, _, _, _ = _displacement_run(cb, T, np.random.default_rng(0))
+    assert not np.array_equal(mb, oracle.assign_int(cb, T)["match_b"])
