@@ -91,6 +91,8 @@ struct Ctl {
     // proposals, donations and the rest, grid barrier; then the item count.
     // prof_own sums CTA 0's values over the rounds, prof_max sums the
     // per-round maximum over CTAs of each segment; prof_rounds counts rounds.
+    // The sequential rule (rule_seq.cuh) uses them per phase: segments key
+    // update, chains, both; prof_own[3] sums the warps per row.
     unsigned long long prof_own[8];
     unsigned long long prof_max[8];
     unsigned long long prof_slot[2][8];  // per round parity: max over CTAs

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_seq(Params p) {
         ++phase;
         const unsigned ph = (unsigned)phase;
         const int W = p.won_words;
+        const unsigned long long t0 = p.profile ? ptimer() : 0;
         // warps per row: the largest power of two <= total warps / rows, in [1, 16]
         int wpr = 1;
         while (wpr < kWarps && (unsigned long long)(2 * wpr) * nf <= (unsigned long long)total_warps) wpr *= 2;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_seq(Params p) {
         unsigned *won = p.won + (size_t)(ph % 3) * W;
         if (threadIdx.x == 0) s_push = 0;
         __syncthreads();
+        const unsigned long long t1 = p.profile ? ptimer() : 0;
 
         int par = 0;
         for (unsigned long long i = (unsigned long long)rank; i < nf; i += (unsigned long long)groups) {
@@ -238,7 +240,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_seq(Params p) {
         }
         __syncthreads();
         const unsigned long long mine = s_push;
+        unsigned long long t2 = 0;
+        if (p.profile && threadIdx.x == 0) {
+            // PR_PROFILE=1: per phase the maximum over CTAs of the key update,
+            // the chains and both, in rotating slots of prof_slot (phase % 3)
+            t2 = ptimer();
+            unsigned long long *slot = &ctl->prof_slot[0][0] + (ph % 3) * 4;
+            atomicMax(slot + 0, t1 - t0);
+            atomicMax(slot + 1, t2 - t1);
+            atomicMax(slot + 2, t2 - t0);
+        }
         if (!grid_sum_barrier(&ctl->bar_slot[0][0], &ctl->head, gen, G, p.spin_limit, mine, sum)) break;
+        if (p.profile && threadIdx.x == 0) {
+            const unsigned long long t3 = ptimer();
+            if (blockIdx.x == 0) {
+                unsigned long long *slot = &ctl->prof_slot[0][0] + (ph % 3) * 4;
+                // the slot read at the previous barrier is written next in phase ph + 2
+                unsigned long long *next = &ctl->prof_slot[0][0] + ((ph + 2) % 3) * 4;
+                for (int k = 0; k < 3; ++k) {
+                    ctl->prof_max[k] += slot[k];
+                    next[k] = 0;
+                }
+                ctl->prof_own[0] += t1 - t0;
+                ctl->prof_own[1] += t2 - t1;
+                ctl->prof_own[2] += t3 - t2;
+                ctl->prof_own[3] += wpr;
+                ctl->prof_rounds += 1;
+            }
+        }
         start = pushed;
         pushed += sum;
         nf = sum;
