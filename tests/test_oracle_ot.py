@@ -111,6 +111,26 @@ def test_returned_duals_are_feasible(seed, eps):
     assert ((r["clo"] + r["chi"]) > 0).any()
 
 
+def test_returned_duals_with_zero_masses():
+    """Zero masses on both sides: a demand of mass 0 has D_a = 0 copies
+    (Sec. 4) and so no dual to check; Eq. 2 holds between every supply's F_b
+    and the highest dual of every demand that has copies."""
+    C, nu, mu = W.ot_euclid_2d(40, 50, 3)
+    nu = nu.copy()
+    nu[[1, 7]] = 0.0
+    nu /= nu.sum()
+    mu = mu.copy()
+    mu[[0, 4, 49]] = 0.0
+    mu /= mu.sum()
+    r = O.ot(C, nu, mu, 0.05)
+    has = (r["clo"] + r["chi"]) > 0
+    assert not has[[0, 4, 49]].any() and has.sum() == 47
+    F = r["F"].astype(np.int64)
+    kmin = r["kmin"].astype(np.int64)
+    top = np.where(r["clo"] > 0, -kmin, -kmin - 1)
+    assert not ((F[:, None] + top[None, :] > r["cbar"].astype(np.int64) + 1) & has[None, :]).any()
+
+
 def test_theta_and_counts_by_hand():
     # n = 3, eps = 0.5: theta = 24; supplies 0.5/0.25/0.25 -> 12/6/6 copies,
     # demands 1/3 each -> ceil(24/3) = 8 copies.
