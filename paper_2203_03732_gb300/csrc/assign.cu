@@ -311,10 +311,13 @@ __device__ __forceinline__ void push_next(Smem &s, int nxt, int keep, int b, int
 // word 1; it then spins (bounded) with acquire loads until the arrival field
 // reaches the grid size.  CTA 0 zeroes slot (h + 2) % 4 during round h: every
 // CTA read it before arriving at barrier h - 1, and barrier h + 2 reuses it.
+// With all_to_pool (no CTA keeps rows: every row of the next phase goes to
+// the pool) the pool total equals the summed nf_delta, so word 1 is neither
+// added to nor read, which saves a dependent load after every barrier.
 // Returns false when the kernel must stop.
 __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsigned G,
                                           long long limit, unsigned long long mine,
-                                          unsigned long long donated) {
+                                          unsigned long long donated, bool all_to_pool) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned h = gen + 1;
@@ -323,7 +326,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
             ctl->bar_slot[(h + 2) & 3][0] = 0;
             ctl->bar_slot[(h + 2) & 3][1] = 0;
         }
-        if (donated)
+        if (donated && !all_to_pool)
             asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(slot + 1), "l"(donated) : "memory");
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(slot), "l"(mine) : "memory");
         unsigned long long v = 0;
@@ -344,7 +347,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
         }
         const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
         s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
-        s.pub2 = ok ? ld_relaxed_u64(slot + 1) : 0;
+        s.pub2 = !ok ? 0 : all_to_pool ? ((v >> 40) & 0xFFFFFFull) : ld_relaxed_u64(slot + 1);
         s.err = ok ? 0 : 1;
     }
     __syncthreads();
@@ -914,7 +917,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 }
             }
             const bool synced = CL ? cluster_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)
-                                   : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated);
+                                   : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated,
+                                               keep == 0);
             if (!synced) goto done;
             if (p.profile && threadIdx.x == 0) {
                 seg[5] = ptimer() - t_r2;
