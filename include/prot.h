@@ -334,7 +334,11 @@ pr_status pr_assign_batched_autotune(const float *XA, const float *XB, int32_t d
 /* Optimal transport (Sec. 4).                                               */
 /* ------------------------------------------------------------------------ */
 
-/* Workspace bytes of pr_ot (0 if the sizes are invalid). */
+/* Workspace bytes of pr_ot (0 if the sizes are invalid): the rounded costs
+ * (n_sup x n_dem, one or two bytes each) and O(n_sup + n_dem) more.  The
+ * matched copy counts are kept in one list per demand (32 entries each,
+ * plus an arena of 8 (n_sup + n_dem) + 4096 entries for longer lists); a
+ * solve whose lists need more arena reports PR_ERR_CAPACITY. */
 size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem);
 
 /*
@@ -361,15 +365,18 @@ size_t pr_ot_workspace(int32_t n_sup, int32_t n_dem);
  *   plan_row, plan_col, plan_mass  [plan_cap] out: the plan as (supply,
  *               demand, mass) triples, each pair at most once
  *   plan_nnz    [1] out: number of triples (also written when > plan_cap,
- *               which returns PR_ERR_CAPACITY)
+ *               which is PR_ERR_CAPACITY)
  *   y_sup       [n_sup] out: dual of the free copies of each supply (its
  *               largest copy dual), units of eps
  *   dem_kmin, dem_lo, dem_hi  [n_dem] out: each demand's copies have duals
  *               -dem_kmin (dem_lo copies) and -dem_kmin - 1 (dem_hi copies)
  *   cost        [1] out: sum of mass * C over the plan (FP64)
  *   stats       host, may be NULL
- * pr_ot synchronises `stream`: the host reads the phase loop's outcome and
- * the plan size before the plan is written.
+ * Like pr_assign, pr_ot only enqueues work on `stream` and synchronises it
+ * iff `stats` is non-NULL; the plan size and every device-side error
+ * (invalid masses or costs, the loop's time-out or phase cap, the plan
+ * exceeding plan_cap, the list arena running out) are found on the device.
+ * With stats == NULL, pr_ws_status(ws, stream) reports them later.
  */
 pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_sup, int32_t n_dem,
                 const double *supply, const double *demand, double eps, int64_t plan_cap,

@@ -61,6 +61,17 @@ def _stream_handle(torch, device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+def ws_status(ws: Workspace | None = None):
+    """Raise PrError if a solve enqueued on `ws` (default: the current
+    device's default workspace) recorded a device-side error; synchronises
+    the current stream (pr_ws_status).  For calls made with sync=False."""
+    torch = _torch()
+    w = ws or _workspace(torch.device("cuda", torch.cuda.current_device()))
+    if w.buf is None:
+        raise ValueError("ws_status: the workspace holds no solve")
+    _lib.check(_lib.load().pr_ws_status(w.buf.data_ptr(), _stream_handle(torch, w.buf.device)), "pr_ws_status")
+
+
 def assign(C, eps: float, *, sync: bool = True, ws: Workspace | None = None, out=None,
            rule: str = "lowest", results_on_device: bool = False, _within: bool = False):
     """Additive eps-approximate assignment (Sec. 2.2 of the paper).
@@ -482,13 +493,17 @@ def assignment_loss(X, Y, eps: float):
     return __getattr__("AssignLoss").apply(X, Y, eps)
 
 
-def ot(C, supply, demand, eps: float, *, plan_cap: int | None = None, ws: Workspace | None = None):
+def ot(C, supply, demand, eps: float, *, plan_cap: int | None = None, ws: Workspace | None = None,
+       sync: bool = True):
     """Additive eps-approximate optimal transport (Sec. 4 of the paper).
 
     C: (n_sup, n_dem) float32/float64 CUDA tensor of costs in [0, 1] (rows =
     supplies); supply, demand: FP64 CUDA tensors of masses summing to 1.
     Returns dict(plan_row, plan_col, plan_mass (the nnz plan triples), cost,
-    y_sup, dem_kmin, dem_lo, dem_hi (cluster duals, units of eps), stats)."""
+    y_sup, dem_kmin, dem_lo, dem_hi (cluster duals, units of eps), stats).
+    sync=False enqueues the solve and returns at once: the plan arrays are
+    then returned at their full capacity with plan_nnz on the device, no
+    stats, and device errors are read later with ws_status(ws)."""
     torch = _torch()
     L = _lib.load()
     if not (C.is_cuda and supply.is_cuda and demand.is_cuda):
@@ -523,9 +538,11 @@ def ot(C, supply, demand, eps: float, *, plan_cap: int | None = None, ws: Worksp
                  float(eps), plan_cap, out["plan_row"].data_ptr(), out["plan_col"].data_ptr(),
                  out["plan_mass"].data_ptr(), out["plan_nnz"].data_ptr(), out["y_sup"].data_ptr(),
                  out["dem_kmin"].data_ptr(), out["dem_lo"].data_ptr(), out["dem_hi"].data_ptr(),
-                 out["cost"].data_ptr(), ctypes.byref(st), wsb.data_ptr(), wsb.numel(),
+                 out["cost"].data_ptr(), ctypes.byref(st) if sync else None, wsb.data_ptr(), wsb.numel(),
                  _stream_handle(torch, dev))
     _lib.check(rc, "pr_ot")
+    if not sync:
+        return out
     nnz = int(out["plan_nnz"].item())
     for k in ("plan_row", "plan_col", "plan_mass"):
         out[k] = out[k][:nnz]

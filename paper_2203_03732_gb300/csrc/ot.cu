@@ -12,13 +12,20 @@
 // cluster the only one that can be admissible, and (a, b) is admissible iff
 // cbar(b,a) + kmin_a == F_b - 1 -- the assignment test with k(a) = kmin_a.
 //
-// Matched copy counts live in two dense planes [a][b]; plane sel[a] holds
-// a's matches at key kmin_a (its "lo" cluster), the other plane those at
-// kmin_a + 1.  When the lo cluster runs out (every match in it was evicted,
-// or it held a's free copies) the planes swap roles: the emptied plane is
-// all zero and becomes the new "hi" plane.  After the loop, k_fix_demand
-// reads each column's two segments once and compacts its nonzero (b, count)
-// pairs into their heads; k_fix_write reads only those.
+// Matched copy counts live in one list per demand a: entries (b, lo, hi),
+// ascending b, each b at most once, where lo counts b's copies matched to a's
+// copies at key kmin_a (a's "lo" cluster) and hi those at kmin_a + 1.  A
+// grant adds to b's hi count (a new entry is inserted in order); an eviction
+// takes lo counts from the end of the list (highest supply index first).
+// When the lo cluster runs out (every match in it was evicted, or it held
+// a's free copies) the clusters shift: every entry's hi count becomes its lo
+// count, and entries left with none are dropped.  A list starts in a fixed
+// slot of 32 entries; a longer list moves to a slot of twice the size from a
+// shared arena (bump allocation, never freed; a list keeps its slot).  The
+// lists hold about as many entries as there are matched (supply, demand)
+// pairs (measured: 0.9 to 1.5 x (n_sup + n_dem) at their largest), so the
+// storage is O(n_sup + n_dem), not n_sup x n_dem.  The plan's matched
+// entries are read straight from the lists after the loop.
 //
 // One phase (B' = supply vertices with free copies), steps of k_ot_loop (one
 // cooperative launch; a grid barrier with a summed payload after each step):
@@ -31,8 +38,10 @@
 //                        highest supply index first (step II)
 //   ot_phase_end    F_b += 1 for b in B' left with unplaced copies (III b);
 //                   clusters shift up where the lo cluster is empty (III a)
-// The host reads the counters once, after the loop (the plan size check
-// then synchronises the stream).
+// Nothing in a solve waits for the host: errors found on the device (masses,
+// costs, the loop, the plan capacity) are recorded in the workspace head, the
+// kernels after them return at once, and the host reads the head only when
+// the caller asks for stats (or later through pr_ws_status).
 //
 // Plan and fix-up (a reading: the paper defers this part to another paper):
 // mass(b,a) = matched copies / theta; a demand that received more than mu_a
@@ -62,8 +71,8 @@ namespace {
 constexpr int kOtThreads = 256;
 constexpr int kOtUnroll = 4;  // 2 KiB warp chunks (swept 3, 4, 8 at 10k x 10k)
 constexpr int kFlagSearching = 1, kFlagInBp = 2;
-constexpr int kFixUnroll = 8;
-constexpr int kCostCtas = 64;  // CTAs of the cost sum (a constant: same order on every device)  // plan-column chunks of 32 counts read at a time
+constexpr int kCostCtas = 64;  // CTAs of the cost sum (a constant: same order on every device)
+constexpr int kListSlot = 32;  // entries of a demand's first list slot (one per lane of a warp)
 
 struct OCtl {
     WsHead head;
@@ -76,17 +85,26 @@ struct OCtl {
     long long bytes;
     unsigned long long mass_units[2];  // sum of floor(m 2^32) over supplies, demands
     unsigned cost_done;                // CTAs of k_fix_cost that have finished
-    unsigned pad2;
+    unsigned arena_top;                // list entries taken from the arena so far
     double cost_part[kCostCtas];       // their partial sums
 };
 
 struct OLayout {
-    size_t ctl, cb, key, S, D, F, f, r, ptr, pa, flag, kmin, clo, chi, avail, sel, granted, prop;
-    size_t plane, nnz_a, off_a, trim_b, trim_t, q, rres, cnt_b, off_b, bsort_a, bsort_m, nw_flag,
+    size_t ctl, cb, key, S, D, F, f, r, ptr, flag, kmin, clo, chi, avail, granted, prop;
+    size_t eb, elo, ehi, seg_off, seg_cap, seg_len;
+    size_t nnz_a, off_a, trim_b, trim_t, q, rres, cnt_b, off_b, bsort_a, nw_flag,
         nw_off, nw_b, nw_a, nw_t, nw_pr, nw_pq, nw_pos, total;
     int ldq;
-    size_t plane_elems;
+    long long arena;      // entries of the list arena
+    long long list_cap;   // entries of all list storage: n_dem first slots + the arena
 };
+
+// The arena holds the lists that outgrow their first slot.  A list of L
+// entries has taken at most 4L arena entries (slots of 64, 128, ... up to 2L),
+// and the lists together hold about (n_sup + n_dem) entries or fewer, so 8 x
+// (n_sup + n_dem) leaves room; a solve that needs more reports
+// PR_ERR_CAPACITY.
+inline long long ot_arena_entries(int nB, int nA) { return 8ll * ((long long)nB + nA) + 4096; }
 
 OLayout make_olayout(int nB, int nA) {
     OLayout L;
@@ -101,17 +119,21 @@ OLayout make_olayout(int nB, int nA) {
     L.f = c.take<int>(nB);
     L.r = c.take<int>(nB);
     L.ptr = c.take<int>(nB);
-    L.pa = c.take<int>(nB);
     L.flag = c.take<int>(nB);
     L.kmin = c.take<int>(nA);
     L.clo = c.take<int>(nA);
     L.chi = c.take<int>(nA);
     L.avail = c.take<int>(nA);
-    L.sel = c.take<int>(nA);
     L.granted = c.take<int>(nA);
     L.prop = c.take<unsigned long long>(nA);
-    L.plane_elems = (size_t)nA * (size_t)nB;
-    L.plane = c.take<int>(2 * L.plane_elems);
+    L.arena = ot_arena_entries(nB, nA);
+    L.list_cap = (long long)nA * kListSlot + L.arena;
+    L.eb = c.take<int>((size_t)L.list_cap);
+    L.elo = c.take<int>((size_t)L.list_cap);
+    L.ehi = c.take<int>((size_t)L.list_cap);
+    L.seg_off = c.take<int>(nA);
+    L.seg_cap = c.take<int>(nA);
+    L.seg_len = c.take<int>(nA);
     L.nnz_a = c.take<int>(nA);
     L.off_a = c.take<int>((size_t)nA + 1);
     L.trim_b = c.take<int>(nA);
@@ -120,8 +142,7 @@ OLayout make_olayout(int nB, int nA) {
     L.rres = c.take<double>(nB);
     L.cnt_b = c.take<int>(nB);
     L.off_b = c.take<int>((size_t)nB + 1);
-    L.bsort_a = L.plane;  // the count planes are dead once the plan is written
-    L.bsort_m = 0;
+    L.bsort_a = c.take<int>((size_t)L.list_cap);  // the plan's matched entries, by supply
     L.nw_flag = c.take<int>((size_t)nB + nA);
     L.nw_off = c.take<int>((size_t)nB + nA + 1);
     L.nw_b = c.take<int>((size_t)nB + nA);
@@ -138,20 +159,16 @@ struct OParams {
     OCtl *ctl;
     const void *cb;  // uint8_t or uint16_t [nB][ldq] (bytes when floor(1/eps) <= 252)
     void *key;       // k = kmin_a per column, in the same type (padding 0xFF / 0x8000)
-    int *S, *D, *F, *f, *r, *ptr, *pa, *flag;
-    int *kmin, *clo, *chi, *avail, *sel, *granted;
+    int *S, *D, *F, *f, *r, *ptr, *flag;
+    int *kmin, *clo, *chi, *avail, *granted;
     unsigned long long *prop;
-    int *plane;
-    size_t plane_elems;
+    // per-demand lists: entry i of a's list is (eb, elo, ehi)[seg_off[a] + i],
+    // i < seg_len[a] <= seg_cap[a]; arena slots start at n_dem * kListSlot
+    int *eb, *elo, *ehi;
+    int *seg_off, *seg_cap, *seg_len;
+    long long list_cap;
     int nB, nA, ldq;
 };
-
-__device__ __forceinline__ int *lo_plane(const OParams &p, int a) {
-    return p.plane + (size_t)p.sel[a] * p.plane_elems + (size_t)a * p.nB;
-}
-__device__ __forceinline__ int *hi_plane(const OParams &p, int a) {
-    return p.plane + (size_t)(p.sel[a] ^ 1) * p.plane_elems + (size_t)a * p.nB;
-}
 
 // S_b = floor(theta nu_b), D_a = ceil(theta mu_a) (Sec. 4), one FP64 product
 // each.  Also sums floor(m 2^32) per side, exactly (each term < 2^33): the
@@ -190,16 +207,19 @@ __global__ void k_ot_counts(const double *nu, const double *mu, int nB, int nA, 
     }
 }
 
+// Runs after k_ot_counts (stream order), so the mass sums are complete: a
+// side whose floor(m 2^32) sum to 1.5 * 2^32 or more is refused here.
 template <class CB>
 __global__ void k_ot_init(OParams p) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && (p.ctl->mass_units[0] >= (3ull << 31) || p.ctl->mass_units[1] >= (3ull << 31)))
+        record_error(&p.ctl->head, PR_ERR_INVALID);
     for (int b = t0; b < p.nB; b += stride) {
         p.F[b] = 1;
         p.f[b] = p.S[b];
         p.r[b] = 0;
         p.ptr[b] = 0;
-        p.pa[b] = -1;
         p.flag[b] = 0;
     }
     for (int a = t0; a < p.ldq; a += stride) {
@@ -209,14 +229,12 @@ __global__ void k_ot_init(OParams p) {
         p.clo[a] = p.D[a];
         p.chi[a] = 0;
         p.avail[a] = p.D[a];
-        p.sel[a] = 0;
         p.granted[a] = 0;
         p.prop[a] = word_of(0, -1);
+        p.seg_off[a] = a * kListSlot;  // every list starts empty in its first slot
+        p.seg_cap[a] = kListSlot;
+        p.seg_len[a] = 0;
     }
-    uint4 *pl = reinterpret_cast<uint4 *>(p.plane);
-    const size_t n4 = (2 * p.plane_elems) / 4;
-    for (size_t i = t0; i < n4; i += stride) pl[i] = make_uint4(0, 0, 0, 0);
-    for (size_t i = n4 * 4 + t0; i < 2 * p.plane_elems; i += stride) p.plane[i] = 0;
 }
 
 __global__ void k_ot_ctl_init(OCtl *c) {
@@ -239,11 +257,10 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long v) {
 __device__ __forceinline__ unsigned long long ot_phase_start(const OParams &p) {
     unsigned long long mine = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x) {
-        const int fb = p.f[b];
+        const int fb = ld_relaxed_s32(p.f + b);  // evictions add to it from any CTA
         p.r[b] = fb;
         p.flag[b] = fb > 0 ? (kFlagSearching | kFlagInBp) : 0;
         p.ptr[b] = 0;
-        p.pa[b] = -1;
         mine += (unsigned long long)fb;
     }
     return mine;
@@ -266,19 +283,20 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
     const CB *key = static_cast<const CB *>(p.key);
     unsigned long long bytes = 0;
     // a row's flag, dual and resume column are loaded together, and the next
-    // row's while this one is scanned (only this warp writes them here)
+    // row's while this one is scanned (only this warp writes them in this
+    // step; other CTAs wrote them in earlier steps, so the loads go to L2)
     int nfl = 0, nF = 0, nst = 0;
     if (warp_g < p.nB) {
-        nfl = p.flag[warp_g];
-        nF = p.F[warp_g];
-        nst = p.ptr[warp_g];
+        nfl = ld_relaxed_s32(p.flag + warp_g);
+        nF = ld_relaxed_s32(p.F + warp_g);
+        nst = ld_relaxed_s32(p.ptr + warp_g);
     }
     for (int b = warp_g; b < p.nB; b += nwarps) {
         const int fl = nfl, Fb = nF, start = nst;
         if (b + nwarps < p.nB) {
-            nfl = p.flag[b + nwarps];
-            nF = p.F[b + nwarps];
-            nst = p.ptr[b + nwarps];
+            nfl = ld_relaxed_s32(p.flag + b + nwarps);
+            nF = ld_relaxed_s32(p.F + b + nwarps);
+            nst = ld_relaxed_s32(p.ptr + b + nwarps);
         }
         if (!(fl & kFlagSearching)) continue;
         const uint32_t tgt = (uint32_t)(Fb - 1);
@@ -325,11 +343,10 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
         if (lane == 0) {
             if (found >= 0) {
                 atomicMax(p.prop + found, word_of(R, b));
-                p.pa[b] = found;
                 p.ptr[b] = found;
                 ++props;
             } else {
-                p.flag[b] &= ~kFlagSearching;
+                atomicAnd(p.flag + b, ~kFlagSearching);
             }
         }
     }
@@ -337,72 +354,195 @@ __device__ __forceinline__ unsigned ot_propose(const OParams &p, unsigned R, uns
     return props;
 }
 
-// Thread per proposer: the winner of a takes g copies.  Grants that take
-// matched lo copies (kmin_a >= 1) go on a CTA list; after a CTA barrier each
-// warp evicts the partners of one listed grant, from the highest supply index
-// down.  Every a has one winner, and the counts other grants also touch (f)
-// change by atomics, so the order of the grants does not matter.  The CTA
-// walks its proposers in waves of blockDim.x, so the list never holds more
-// than blockDim.x grants.
-__device__ __forceinline__ void ot_grant(const OParams &p) {
-    __shared__ int ev_a[kOtThreads], ev_need[kOtThreads];
-    __shared__ int n_ev;
+// ---------------------------------------------------------------------------
+// Per-demand lists (warp operations; only the grant or the phase end of
+// demand a touches a's list, one warp at a time)
+// ---------------------------------------------------------------------------
+// Step (II): take `need` lo copies from a's list, highest supply index first
+// (the end of the list); each copy taken rejoins its supply's free copies.
+__device__ __forceinline__ void list_evict(const OParams &p, int a, int need, int lane) {
+    const int off = p.seg_off[a], n = p.seg_len[a];
+    int taken = 0;  // lo copies of the entries above this chunk
+    for (int top = n - 1; top >= 0 && taken < need; top -= 32) {
+        const int i = top - lane;  // lane 0: the highest remaining entry
+        const int c = i >= 0 ? p.elo[off + i] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int t = need - (taken + incl - c);
+        t = t < 0 ? 0 : (t > c ? c : t);
+        if (t > 0) {
+            p.elo[off + i] = c - t;
+            atomicAdd(p.f + p.eb[off + i], t);
+        }
+        taken += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+}
+
+// g copies of b matched to a's hi cluster: added to b's entry, or a new entry
+// inserted in ascending order (the list moves to a slot twice its size from
+// the arena when full).  Returns false when the arena is spent.
+__device__ __forceinline__ bool list_add_hi(const OParams &p, int a, int b, int g, int lane) {
+    int off = p.seg_off[a];
+    const int n = p.seg_len[a];
+    int pos = n, at = -1;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int i = c0 + lane;
+        const int bb = i < n ? p.eb[off + i] : 0x7FFFFFFF;
+        const unsigned eq = __ballot_sync(0xFFFFFFFFu, bb == b);
+        if (eq) {
+            at = c0 + __ffs(eq) - 1;
+            break;
+        }
+        const unsigned gt = __ballot_sync(0xFFFFFFFFu, bb > b);
+        if (gt) {
+            pos = c0 + __ffs(gt) - 1;
+            break;
+        }
+    }
+    if (at >= 0) {
+        if (lane == 0) p.ehi[off + at] += g;
+        return true;
+    }
+    const int cap = p.seg_cap[a];
+    if (n == cap) {  // move to a slot of 2 cap entries
+        long long o2 = 0;
+        if (lane == 0) o2 = (long long)atomicAdd(&p.ctl->arena_top, 2u * (unsigned)cap);
+        o2 = __shfl_sync(0xFFFFFFFFu, o2, 0);
+        const long long base = (long long)p.nA * kListSlot + o2;
+        if (base + 2ll * cap > p.list_cap) {
+            if (lane == 0) record_error(&p.ctl->head, PR_ERR_CAPACITY);
+            return false;
+        }
+        for (int i = lane; i < n; i += 32) {
+            p.eb[base + i] = p.eb[off + i];
+            p.elo[base + i] = p.elo[off + i];
+            p.ehi[base + i] = p.ehi[off + i];
+        }
+        __syncwarp();
+        off = (int)base;
+        if (lane == 0) {
+            p.seg_off[a] = off;
+            p.seg_cap[a] = 2 * cap;
+        }
+    }
+    // entries pos .. n - 1 move up by one, the last chunk first (every lane
+    // reads its entry before any lane of the warp writes)
+    for (int top = n - 1; top >= pos; top -= 32) {
+        const int i = top - lane;
+        const bool act = i >= pos;
+        int vb = 0, vl = 0, vh = 0;
+        if (act) {
+            vb = p.eb[off + i];
+            vl = p.elo[off + i];
+            vh = p.ehi[off + i];
+        }
+        __syncwarp();
+        if (act) {
+            p.eb[off + i + 1] = vb;
+            p.elo[off + i + 1] = vl;
+            p.ehi[off + i + 1] = vh;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        p.eb[off + pos] = b;
+        p.elo[off + pos] = 0;
+        p.ehi[off + pos] = g;
+        p.seg_len[a] = n + 1;
+    }
+    return true;
+}
+
+// Step (III a) on a's list when its clusters shift up: the lo counts are all
+// zero (the lo cluster ran out), every hi count becomes the lo count, and
+// entries left with no copies are dropped (the order is kept).
+__device__ __forceinline__ void list_shift(const OParams &p, int a, int lane) {
+    const int off = p.seg_off[a], n = p.seg_len[a];
+    int w = 0;
+    bool bad = false;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int i = c0 + lane;
+        int bb = 0, hh = 0;
+        if (i < n) {
+            bb = p.eb[off + i];
+            hh = p.ehi[off + i];
+            bad |= p.elo[off + i] != 0;
+        }
+        const unsigned keep = __ballot_sync(0xFFFFFFFFu, hh > 0);
+        __syncwarp();
+        if (hh > 0) {
+            const int k = off + w + __popc(keep & ((1u << lane) - 1));
+            p.eb[k] = bb;
+            p.elo[k] = hh;
+            p.ehi[k] = 0;
+        }
+        w += __popc(keep);
+        __syncwarp();
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) record_error(&p.ctl->head, PR_ERR_INTERNAL);
+    if (lane == 0) p.seg_len[a] = w;
+}
+
+// The demands of one wave of the grid, CTA-minor: thread t of CTA c takes
+// demand c + t * G, so every CTA gets about n_dem / G of them.
+__device__ __forceinline__ int wave_demand(int base, unsigned G) {
+    return base + (int)(threadIdx.x * G + blockIdx.x);
+}
+
+// Grant step: thread per demand a that received a proposal in round R; its
+// lowest proposer b takes g = min(r_b, avail_a) copies.  The grants go on a
+// CTA list; after a CTA barrier each warp takes one listed grant: if a's
+// copies are matched (kmin_a >= 1) it evicts g of them (step II), then it
+// adds b's g copies to a's list.  Every a has one winner and touches only its
+// own list, and the counts other grants also touch (f) change by atomics, so
+// the order of the grants does not matter.
+__device__ __forceinline__ void ot_grant(const OParams &p, unsigned R) {
+    __shared__ int gl_a[kOtThreads], gl_b[kOtThreads], gl_g[kOtThreads];
+    __shared__ int n_gl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int base = blockIdx.x * blockDim.x; base < p.nB; base += gridDim.x * blockDim.x) {
-        if (threadIdx.x == 0) n_ev = 0;
+    const unsigned G = gridDim.x;
+    for (int base = 0; base < p.nA; base += (int)(G * blockDim.x)) {
+        if (threadIdx.x == 0) n_gl = 0;
         __syncthreads();
-        const int b = base + threadIdx.x;
-        const int a = b < p.nB ? p.pa[b] : -1;
-        if (a >= 0) {
-            p.pa[b] = -1;
-            // the winner test and the values a winner needs, loaded at once
-            // (only a's winner writes them in this step)
-            const unsigned long long w = p.prop[a];
-            const int av = p.avail[a];
-            const int rb = p.r[b];
-            const int km = p.kmin[a];
-            int *hp = hi_plane(p, a) + b;
-            if (row_of(w) == b) {
+        const int a = wave_demand(base, G);
+        if (a < p.nA) {
+            // the column's word and the winner's remaining copies were written
+            // by other CTAs: coherent loads (L2), never a line this SM's L1
+            // kept from an earlier round
+            const unsigned long long w = ld_relaxed_u64(p.prop + a);
+            if (tag_of(w) == R) {
+                const int b = row_of(w);
+                // the values a winner needs, loaded at once (only a's winner
+                // writes them in this step)
+                const int av = p.avail[a];
+                const int rb = ld_relaxed_s32(p.r + b);
+                const int km = p.kmin[a];
                 const int g = rb < av ? rb : av;
                 p.avail[a] = av - g;
                 p.r[b] = rb - g;
-                if (rb - g == 0) p.flag[b] &= ~kFlagSearching;
+                if (rb - g == 0) atomicAnd(p.flag + b, ~kFlagSearching);
                 p.clo[a] -= g;
                 p.chi[a] += g;
                 p.granted[a] = 1;
-                *hp += g;
                 atomicSub(p.f + b, g);
-                if (km >= 1 && g > 0) {
-                    const int k = atomicAdd(&n_ev, 1);
-                    ev_a[k] = a;
-                    ev_need[k] = g;
+                if (g > 0) {
+                    const int k = atomicAdd(&n_gl, 1);
+                    gl_a[k] = a;
+                    gl_b[k] = b;
+                    gl_g[k] = km >= 1 ? -g : g;  // negative: matched copies are taken
                 }
             }
         }
         __syncthreads();
-        // step (II): evict `need` lo-cluster partners, highest supply index first
-        for (int e = warp; e < n_ev; e += nw) {
-            int *lo = lo_plane(p, ev_a[e]);
-            int need = ev_need[e];
-            for (int top = p.nB - 1; top >= 0 && need > 0; top -= 32) {
-                const int b2 = top - lane;
-                const int c = b2 >= 0 ? lo[b2] : 0;
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int before = incl - c;
-                int t = need - before;
-                t = t < 0 ? 0 : (t > c ? c : t);
-                if (t > 0) {
-                    lo[b2] = c - t;
-                    atomicAdd(p.f + b2, t);
-                }
-                const int chunk_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                need -= chunk_total < need ? chunk_total : need;
-            }
+        for (int e = warp; e < n_gl; e += nw) {
+            const int ga = gl_a[e], gg = gl_g[e];
+            if (gg < 0) list_evict(p, ga, -gg, lane);
+            __syncwarp();
+            list_add_hi(p, ga, gl_b[e], gg < 0 ? -gg : gg, lane);
         }
         __syncthreads();
     }
@@ -410,22 +550,33 @@ __device__ __forceinline__ void ot_grant(const OParams &p) {
 
 template <class CB>
 __device__ __forceinline__ void ot_phase_end(const OParams &p) {
+    __shared__ int sh_a[kOtThreads];
+    __shared__ int n_sh;
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned G = gridDim.x;
     for (int b = t0; b < p.nB; b += stride)
-        if ((p.flag[b] & kFlagInBp) && p.r[b] > 0) p.F[b] += 1;  // step (III b)
-    for (int a = t0; a < p.nA; a += stride) {
-        if (!p.granted[a]) continue;
-        p.granted[a] = 0;
-        if (p.clo[a] == 0 && p.chi[a] > 0) {  // step (III a): clusters shift up
-            const int k = p.kmin[a] + 1;
-            p.kmin[a] = k;
-            static_cast<CB *>(p.key)[a] = (CB)k;  // bytes: k <= floor(1/eps) + 2 <= 254
-            p.clo[a] = p.chi[a];
-            p.chi[a] = 0;
-            p.sel[a] ^= 1;
+        if ((ld_relaxed_s32(p.flag + b) & kFlagInBp) && ld_relaxed_s32(p.r + b) > 0) p.F[b] += 1;  // step (III b)
+    for (int base = 0; base < p.nA; base += (int)(G * blockDim.x)) {
+        if (threadIdx.x == 0) n_sh = 0;
+        __syncthreads();
+        const int a = wave_demand(base, G);
+        if (a < p.nA && p.granted[a]) {
+            p.granted[a] = 0;
+            if (p.clo[a] == 0 && p.chi[a] > 0) {  // step (III a): clusters shift up
+                const int k = p.kmin[a] + 1;
+                p.kmin[a] = k;
+                static_cast<CB *>(p.key)[a] = (CB)k;  // bytes: k <= floor(1/eps) + 2 <= 254
+                p.clo[a] = p.chi[a];
+                p.chi[a] = 0;
+                sh_a[atomicAdd(&n_sh, 1)] = a;
+            }
+            p.avail[a] = p.clo[a];
         }
-        p.avail[a] = p.clo[a];
+        __syncthreads();
+        for (int e = warp; e < n_sh; e += nw) list_shift(p, sh_a[e], lane);
+        __syncthreads();
     }
 }
 
@@ -469,13 +620,22 @@ __global__ void __launch_bounds__(kOtThreads, 4) k_ot_loop(OParams p, double eps
             break;
         }
         ++phases;
+        // Every round grants some column's lowest proposer g > 0 copies,
+        // which either places all of b's remaining copies (at most |B'|
+        // times a phase) or uses up a's available copies (at most n_dem
+        // times): a phase has at most n_sup + n_dem rounds with a proposal.
+        long long phase_rounds = 0;
         for (;;) {
             ++R;
+            if (++phase_rounds > (long long)p.nB + p.nA + 1) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) record_error(&c->head, PR_ERR_INTERNAL);
+                return;
+            }
             const unsigned long long np = cta_sum(ot_propose<CB, F7>(p, R, bytes));
             if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, np, sum)) return;
             if (sum == 0) break;
             ++rounds;
-            ot_grant(p);
+            ot_grant(p, R);
             if (!grid_sum_barrier(c->bar, &c->head, gen, G, spin_limit, 0, sum)) return;
         }
         ot_phase_end<CB>(p);
@@ -508,48 +668,34 @@ struct FixParams {
 };
 
 // Warp per demand a: nonzero count, the trim of its highest supplier, and the
-// remaining capacity q_a = max(0, mu_a - received), sums in ascending b.
-// The column's nonzero pairs are also compacted in place: the k-th (in
-// ascending b) leaves its b at lo[k] and its count at hi[k] of a's own plane
-// segments.  k <= b, and a warp writes only after it has read its whole group
-// of kFixUnroll chunks, so no count is overwritten before it is read.
+// remaining capacity q_a = max(0, mu_a - received), sums in ascending b (the
+// order of a's list).
 __global__ void __launch_bounds__(kOtThreads) k_fix_demand(FixParams fp) {
     const OParams &p = fp.o;
+    if (ld_relaxed_s32(&p.ctl->head.err) != 0) return;
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = warp_g; a < p.nA; a += nwarps) {
-        int *lo = lo_plane(p, a), *hi = hi_plane(p, a);
+        const int off = p.seg_off[a], n = p.seg_len[a];
         int nnz = 0, last = -1;
         double recv = 0.0, before_last = 0.0, m_last = 0.0;
-        for (int g0 = 0; g0 < p.nB; g0 += 32 * kFixUnroll) {
-            int cs[kFixUnroll];  // kFixUnroll chunks of 32 counts in flight
-#pragma unroll
-            for (int u = 0; u < kFixUnroll; ++u) {
-                const int b = g0 + 32 * u + lane;
-                cs[u] = b < p.nB ? lo[b] + hi[b] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < kFixUnroll; ++u) {
-                const int b0 = g0 + 32 * u, c = cs[u];
-                const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
-                if (!nz) continue;
-                if (c) {
-                    const int k = nnz + __popc(nz & ((1u << lane) - 1));
-                    lo[k] = b0 + lane;
-                    hi[k] = c;
-                }
-                nnz += __popc(nz);
-                const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
-                // lane order = ascending b: fold the chunk's masses in that order
-                for (unsigned w = nz; w; w &= w - 1) {
-                    const int L = __ffs(w) - 1;
-                    const double mi = __shfl_sync(0xFFFFFFFFu, m, L);
-                    before_last = recv;
-                    m_last = mi;
-                    recv = __dadd_rn(recv, mi);
-                    last = b0 + L;
-                }
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int i = c0 + lane;
+            const int c = i < n ? p.elo[off + i] + p.ehi[off + i] : 0;
+            const int bb = i < n ? p.eb[off + i] : 0;
+            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (!nz) continue;
+            nnz += __popc(nz);
+            const double m = c ? __ddiv_rn((double)c, fp.theta) : 0.0;
+            // lane order = ascending b: fold the chunk's masses in that order
+            for (unsigned w = nz; w; w &= w - 1) {
+                const int L = __ffs(w) - 1;
+                const double mi = __shfl_sync(0xFFFFFFFFu, m, L);
+                before_last = recv;
+                m_last = mi;
+                recv = __dadd_rn(recv, mi);
+                last = __shfl_sync(0xFFFFFFFFu, bb, L);
             }
         }
         if (lane == 0) {
@@ -618,34 +764,51 @@ __global__ void k_prefix(const int *cnt, int n, int *out) {
     if (threadIdx.x == 0) out[n] = carry;
 }
 
-// Warp per demand a: write a's plan entries (b ascending) at off_a[a] from
-// the nnz_a[a] pairs that k_fix_demand compacted into a's plane segments;
-// count the entries of every supply row.
-__global__ void __launch_bounds__(kOtThreads) k_fix_write(FixParams fp) {
+// Warp per demand a: write a's plan entries (b ascending, the order of a's
+// list) at off_a[a]; count the entries of every supply row.  When the matched
+// entries alone exceed plan_cap, PR_ERR_CAPACITY is recorded with their
+// count in plan_nnz, and the kernels after this one return at once.
+__global__ void __launch_bounds__(kOtThreads) k_fix_write(FixParams fp, int64_t *plan_nnz) {
     const OParams &p = fp.o;
+    if (ld_relaxed_s32(&p.ctl->head.err) != 0) return;
+    const int total = fp.off_a[p.nA];
+    if (total > fp.plan_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *plan_nnz = total;
+            record_error(&p.ctl->head, PR_ERR_CAPACITY);
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = warp_g; a < p.nA; a += nwarps) {
-        const int *pb = lo_plane(p, a), *pc = hi_plane(p, a);
-        const int n = fp.nnz_a[a], base = fp.off_a[a], tb = fp.trim_b[a];
-        for (int i = lane; i < n; i += 32) {
-            const int b = pb[i];
-            double m = __ddiv_rn((double)pc[i], fp.theta);
-            if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
-            const long long k = (long long)base + i;
-            if (k < fp.plan_cap) {
-                fp.plan_row[k] = b;
-                fp.plan_col[k] = a;
-                fp.plan_mass[k] = m;
+        const int off = p.seg_off[a], n = p.seg_len[a];
+        const int tb = fp.trim_b[a];
+        int k = fp.off_a[a];
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int i = c0 + lane;
+            const int c = i < n ? p.elo[off + i] + p.ehi[off + i] : 0;
+            const unsigned nz = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (c) {
+                const int b = p.eb[off + i];
+                double m = __ddiv_rn((double)c, fp.theta);
+                if (b == tb) m = __dsub_rn(m, fp.trim_t[a]);
+                const int kk = k + __popc(nz & ((1u << lane) - 1));
+                fp.plan_row[kk] = b;
+                fp.plan_col[kk] = a;
+                fp.plan_mass[kk] = m;
+                atomicAdd(fp.cnt_b + b, 1);
             }
-            atomicAdd(fp.cnt_b + b, 1);
+            k += __popc(nz);
         }
     }
 }
 
 // Thread per entry: scatter the entry index into its supply row's segment.
-__global__ void k_fix_bscatter(FixParams fp, int nnz, int *fill) {
+__global__ void k_fix_bscatter(FixParams fp, int *fill) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
+    const int nnz = fp.off_a[fp.o.nA];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
         const int b = fp.plan_row[k];
         fp.bsort_a[fp.off_b[b] + atomicAdd(fill + b, 1)] = k;
@@ -656,6 +819,7 @@ __global__ void k_fix_bscatter(FixParams fp, int nnz, int *fill) {
 // row's small segment), then rres_b = max(0, nu_b - sent_b).
 __global__ void k_fix_supply(FixParams fp) {
     const OParams &p = fp.o;
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nB; b += gridDim.x * blockDim.x) {
         const int s = fp.off_b[b], e = fp.off_b[b + 1];
         int *seg = fp.bsort_a + s;
@@ -706,6 +870,7 @@ __device__ __forceinline__ int nw_count_lt(const unsigned long long *P, int n, u
 // and demands (CTA 1).  Each thread sums one contiguous run, one scan over
 // the threads gives its offset, then the run is written.
 __global__ void __launch_bounds__(1024) k_nw_prefix(FixParams fp) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     __shared__ unsigned long long warp_off[32];
     const bool dem = blockIdx.x == 1;
     const double *x = dem ? fp.q : fp.rres;
@@ -750,6 +915,7 @@ __global__ void __launch_bounds__(1024) k_nw_prefix(FixParams fp) {
 // the supply's.  flag[place] marks the allocation; the merged order is the
 // serial walk's order.
 __global__ void k_nw_flags(FixParams fp, int *flag, int *place) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     const int nB = fp.o.nB, nA = fp.o.nA;
     const unsigned long long *Pr = fp.nw_pr, *Pq = fp.nw_pq;
     const unsigned long long cap = Pr[nB - 1] < Pq[nA - 1] ? Pr[nB - 1] : Pq[nA - 1];
@@ -780,6 +946,7 @@ __global__ void k_nw_flags(FixParams fp, int *flag, int *place) {
 // the demand run j with Pq[j-1] <= s < Pq[j], a demand start in the supply
 // run i likewise; the allocation ends at min(Pr[i], Pq[j]).
 __global__ void k_nw_write(FixParams fp, const int *flag, const int *place, const int *off, OCtl *ctl) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     const int nB = fp.o.nB, nA = fp.o.nA;
     const unsigned long long *Pr = fp.nw_pr, *Pq = fp.nw_pq;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nB + nA; k += gridDim.x * blockDim.x) {
@@ -808,6 +975,7 @@ __global__ void k_nw_write(FixParams fp, const int *flag, const int *place, cons
 // Thread per north-west allocation: add it to the matched entry of (b, a)
 // (binary search in a's segment, ascending b), or flag it as a new entry.
 __global__ void k_fix_merge(FixParams fp, OCtl *ctl, int *flag) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     const int n = ctl->n_nw;
     const int total = fp.o.nB + fp.o.nA;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -832,8 +1000,10 @@ __global__ void k_fix_merge(FixParams fp, OCtl *ctl, int *flag) {
     }
 }
 
-// New pairs go after the matched entries, in north-west order.
-__global__ void k_fix_append(FixParams fp, OCtl *ctl, const int *flag, const int *off) {
+// New pairs go after the matched entries, in north-west order.  A plan that
+// then exceeds plan_cap records PR_ERR_CAPACITY with its size in plan_nnz.
+__global__ void k_fix_append(FixParams fp, OCtl *ctl, const int *flag, const int *off, int64_t *plan_nnz) {
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     const int n = ctl->n_nw;
     const int nnz = fp.off_a[fp.o.nA];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -845,7 +1015,14 @@ __global__ void k_fix_append(FixParams fp, OCtl *ctl, const int *flag, const int
             fp.plan_mass[pos] = fp.nw_t[k];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_extra = off[fp.o.nB + fp.o.nA];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int extra = off[fp.o.nB + fp.o.nA];
+        ctl->n_extra = extra;
+        if ((long long)nnz + extra > fp.plan_cap) {
+            *plan_nnz = (long long)nnz + extra;
+            record_error(&ctl->head, PR_ERR_CAPACITY);
+        }
+    }
 }
 
 // cost = sum mass * c over the plan in a fixed order: kCostCtas CTAs each
@@ -856,6 +1033,7 @@ __global__ void __launch_bounds__(256)
 k_fix_cost(FixParams fp, const T *C, long long ldc, OCtl *ctl, int64_t *plan_nnz, double *cost) {
     __shared__ double part[256];
     __shared__ bool last;
+    if (ld_relaxed_s32(&fp.o.ctl->head.err) != 0) return;
     const int nnz = fp.off_a[fp.o.nA] + ctl->n_extra;
     const int lim = nnz < fp.plan_cap ? nnz : (int)fp.plan_cap;
     const int per = (lim + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -947,17 +1125,20 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     p.f = (int *)(w + L.f);
     p.r = (int *)(w + L.r);
     p.ptr = (int *)(w + L.ptr);
-    p.pa = (int *)(w + L.pa);
     p.flag = (int *)(w + L.flag);
     p.kmin = (int *)(w + L.kmin);
     p.clo = (int *)(w + L.clo);
     p.chi = (int *)(w + L.chi);
     p.avail = (int *)(w + L.avail);
-    p.sel = (int *)(w + L.sel);
     p.granted = (int *)(w + L.granted);
     p.prop = (unsigned long long *)(w + L.prop);
-    p.plane = (int *)(w + L.plane);
-    p.plane_elems = L.plane_elems;
+    p.eb = (int *)(w + L.eb);
+    p.elo = (int *)(w + L.elo);
+    p.ehi = (int *)(w + L.ehi);
+    p.seg_off = (int *)(w + L.seg_off);
+    p.seg_cap = (int *)(w + L.seg_cap);
+    p.seg_len = (int *)(w + L.seg_len);
+    p.list_cap = L.list_cap;
     p.nB = nB;
     p.nA = nA;
     p.ldq = L.ldq;
@@ -1008,18 +1189,6 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         void *args[] = {(void *)&p, (void *)&eps, (void *)&limit};
         PR_CUDA(cudaLaunchCooperativeKernel(loop, dim3(grid), dim3(kOtThreads), args, 0, st));
     }
-    OCtl h;
-    PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
-    PR_CUDA(cudaStreamSynchronize(st));
-    if (h.head.err == PR_ERR_INVALID) return fail(PR_ERR_INVALID, "pr_ot: invalid costs or masses");
-    if (h.mass_units[0] >= (3ull << 31) || h.mass_units[1] >= (3ull << 31))
-        return fail(PR_ERR_INVALID, "pr_ot: the supply and the demand masses must each sum to 1 "
-                                    "(a side summing to more than 1.5 is refused)");
-    if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
-    const long long phases = h.phases, rounds = h.rounds, free_at_stop = h.free_at_stop, T = h.threshold;
-    pr_status rc = PR_OK;
-    if (rc != PR_OK) return rc;
-
     // plan and fix-up
     FixParams fp;
     fp.o = p;
@@ -1048,21 +1217,12 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     PR_CUDA(cudaGetLastError());
     k_prefix<<<1, 1024, 0, st>>>(fp.nnz_a, nA, fp.off_a);
     PR_CUDA(cudaGetLastError());
-    int nnz = 0;
-    PR_CUDA(cudaMemcpyAsync(&nnz, fp.off_a + nA, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PR_CUDA(cudaStreamSynchronize(st));
-    if (nnz > plan_cap) {
-        const long long v = nnz;
-        PR_CUDA(cudaMemcpyAsync(plan_nnz, &v, sizeof(v), cudaMemcpyHostToDevice, st));
-        PR_CUDA(cudaStreamSynchronize(st));
-        return fail(PR_ERR_CAPACITY, "pr_ot: %d plan entries exceed plan_cap", nnz);
-    }
     k_zero_int<<<g1, 256, 0, st>>>(fp.cnt_b, nB);
-    k_fix_write<<<gw, kOtThreads, 0, st>>>(fp);
+    k_fix_write<<<gw, kOtThreads, 0, st>>>(fp, plan_nnz);
     PR_CUDA(cudaGetLastError());
     k_prefix<<<1, 1024, 0, st>>>(fp.cnt_b, nB, fp.off_b);
     k_zero_int<<<g1, 256, 0, st>>>(fp.cnt_b, nB);
-    k_fix_bscatter<<<g1, 256, 0, st>>>(fp, nnz, fp.cnt_b);
+    k_fix_bscatter<<<g1, 256, 0, st>>>(fp, fp.cnt_b);
     k_fix_supply<<<(nB + 255) / 256, 256, 0, st>>>(fp);
     PR_CUDA(cudaGetLastError());
     {
@@ -1080,7 +1240,7 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
         k_fix_merge<<<g1, 256, 0, st>>>(fp, p.ctl, flag);
         PR_CUDA(cudaGetLastError());
         k_prefix<<<1, 1024, 0, st>>>(flag, nB + nA, off);
-        k_fix_append<<<g1, 256, 0, st>>>(fp, p.ctl, flag, off);
+        k_fix_append<<<g1, 256, 0, st>>>(fp, p.ctl, flag, off, plan_nnz);
         PR_CUDA(cudaGetLastError());
     }
     if (dt == PR_F64)
@@ -1090,22 +1250,30 @@ extern "C" pr_status pr_ot(const void *C, pr_dtype dt, int64_t ldc, int32_t n_su
     PR_CUDA(cudaGetLastError());
     k_ot_duals<<<g1, 256, 0, st>>>(p, y_sup, dem_kmin, dem_lo, dem_hi);
     PR_CUDA(cudaGetLastError());
+    if (!stats) return PR_OK;  // asynchronous: device errors through pr_ws_status
+    OCtl h;
     PR_CUDA(cudaMemcpyAsync(&h, p.ctl, sizeof(OCtl), cudaMemcpyDeviceToHost, st));
     PR_CUDA(cudaStreamSynchronize(st));
-    if ((long long)nnz + h.n_extra > plan_cap)
-        return fail(PR_ERR_CAPACITY, "pr_ot: %lld plan entries exceed plan_cap", (long long)nnz + h.n_extra);
-    if (stats) {
-        stats->phases = phases;
-        stats->rounds = rounds;
-        stats->bytes_scanned = h.bytes;
-        stats->rows_scanned = 0;
-        stats->free_at_stop = (int32_t)free_at_stop;
-        stats->threshold = (int32_t)T;
-        stats->loop_ctas = 0;
-        stats->loop_cluster = 0;
-        stats->cells_examined = 0;
-        stats->barriers = 0;
-    }
+    stats->phases = h.phases;
+    stats->rounds = h.rounds;
+    stats->bytes_scanned = h.bytes;
+    stats->rows_scanned = 0;
+    stats->free_at_stop = (int32_t)h.free_at_stop;
+    stats->threshold = (int32_t)h.threshold;
+    stats->loop_ctas = 0;
+    stats->loop_cluster = 0;
+    stats->cells_examined = 0;
+    stats->barriers = 0;
+    if (h.head.err == PR_ERR_INVALID && (h.mass_units[0] >= (3ull << 31) || h.mass_units[1] >= (3ull << 31)))
+        return fail(PR_ERR_INVALID, "pr_ot: the supply and the demand masses must each sum to 1 "
+                                    "(a side summing to more than 1.5 is refused)");
+    if (h.head.err == PR_ERR_INVALID) return fail(PR_ERR_INVALID, "pr_ot: invalid costs or masses");
+    if (h.head.err == PR_ERR_CAPACITY && h.arena_top > (unsigned)L.arena)
+        return fail(PR_ERR_CAPACITY, "pr_ot: the per-demand lists need more than the workspace's %lld arena entries",
+                    (long long)L.arena);
+    if (h.head.err == PR_ERR_CAPACITY)
+        return fail(PR_ERR_CAPACITY, "pr_ot: the plan exceeds plan_cap (%lld entries; plan_nnz holds the size)",
+                    (long long)plan_cap);
     if (h.head.err) return fail((pr_status)h.head.err, "pr_ot: device reported %s", pr_status_string((pr_status)h.head.err));
     return PR_OK;
 }

@@ -176,3 +176,16 @@ def test_assign_within_refuses_delta_without_gpu(libpath):
                                 ctypes.byref(st), None, 0, None)
         assert rc == _lib.PR_ERR_INVALID
         assert b"delta" in L.pr_last_error()
+
+
+def test_ot_workspace_is_linear_beyond_the_rounded_costs(libpath):
+    """pr_ot keeps its matched copy counts in per-demand lists: apart from
+    the rounded costs (n_sup x ldq 16-bit values at most) the workspace grows
+    like n_sup + n_dem, not n_sup x n_dem."""
+    L = ctypes.CDLL(libpath)
+    L.pr_ot_workspace.restype = ctypes.c_size_t
+    L.pr_ot_workspace.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    for nB, nA in ((10000, 10000), (2000, 30000), (30000, 2000), (1, 1)):
+        ldq = (nA + 15) // 16 * 16
+        rest = L.pr_ot_workspace(nB, nA) - 2 * nB * ldq
+        assert 0 < rest <= 1024 * (nB + nA) + (1 << 20), (nB, nA, rest)

@@ -183,3 +183,49 @@ def test_ot_sixteen_bit_storage(prot, nB, nA):
     C, nu, mu = W.ot_euclid_2d(nB, nA, 13)
     r, dense = gpu_ot(prot, C, nu, mu, 0.003)
     assert_ot_parity(r, dense, O.ot(C, nu, mu, 0.003))
+
+
+def test_ot_async_enqueue(prot):
+    """sync=False: pr_ot only enqueues (no stats); after the stream is done
+    the plan, cost and duals equal the oracle's, and pr_ws_status reports no
+    device error."""
+    import torch
+    C, nu, mu = W.ot_euclid_2d(300, 257, 31)
+    ws = prot.Workspace()
+    r = prot.ot(torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.05,
+                ws=ws, sync=False)
+    assert "stats" not in r
+    prot.ws_status(ws)
+    nnz = int(r["plan_nnz"].item())
+    ref = O.ot(C, nu, mu, 0.05)
+    dense = np.zeros(C.shape)
+    dense[r["plan_row"][:nnz].cpu().numpy(), r["plan_col"][:nnz].cpu().numpy()] = r["plan_mass"][:nnz].cpu().numpy()
+    assert np.array_equal(dense, ref["mass"])
+    assert np.array_equal(r["y_sup"].cpu().numpy(), ref["F"])
+    assert np.array_equal(r["dem_kmin"].cpu().numpy(), ref["kmin"])
+    assert abs(float(r["cost"].cpu()) - ref["cost"]) <= 1e-12 * abs(ref["cost"])
+
+
+@pytest.mark.parametrize("sync", [True, False])
+def test_ot_plan_capacity_found_on_the_device(prot, sync):
+    """A plan_cap below the plan's size: PR_ERR_CAPACITY (at once with stats,
+    from pr_ws_status without), plan_nnz then holds more than plan_cap, and
+    the next solve on the same workspace is exact."""
+    import torch
+    C, nu, mu = W.ot_euclid_2d(120, 90, 32)
+    ref = O.ot(C, nu, mu, 0.05)
+    need = int((ref["mass"] != 0).sum())
+    args = (torch.from_numpy(C).cuda(), torch.from_numpy(nu).cuda(), torch.from_numpy(mu).cuda(), 0.05)
+    ws = prot.Workspace()
+    for cap in (need // 2, need - 1):
+        with pytest.raises(prot.PrError) as e:
+            r = prot.ot(*args, plan_cap=cap, ws=ws, sync=sync)
+            if not sync:
+                prot.ws_status(ws)
+        assert e.value.status == -6
+        if not sync:
+            assert int(r["plan_nnz"].item()) > cap
+    r, dense = gpu_ot(prot, C, nu, mu, 0.05)
+    assert_ot_parity(r, dense, ref)
+    r = prot.ot(*args, plan_cap=need, ws=ws)
+    assert int(r["plan_nnz"].item()) == need
