@@ -38,7 +38,6 @@ constexpr int kMaxCbarByte = 252;         // byte storage when floor(1/eps) <= 2
 struct BDesc {
     long long cb_off;  // element offset of the rounded costs (row stride ldq)
     long long c_off;   // element offset of the cost matrix (matrix source)
-    long long g_off;   // first 8-column group in the flat quantise index
     long long cap;     // phase cap
     int n;
     int ldq;
@@ -92,62 +91,78 @@ struct BParams {
     int64_t *phases;
 };
 
-// Flat index g of an 8-column group -> problem (binary search on g_off).
-__device__ __forceinline__ int problem_of(const BDesc *d, int P, long long g) {
+// ---------------------------------------------------------------------------
+// Rounding of the packed matrices (Eq. 1, exact).
+// ---------------------------------------------------------------------------
+// Padding of the stored type: uint16 0x7FFF or, when floor(1/eps) <= 252, byte 0xFF.
+template <class CB> constexpr uint32_t kPadOf = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
+
+// Every kernel below takes the rows of all problems in one sweep: warp w takes
+// global rows w, w + W, ... (global row r is row r - v_off_i of the problem i
+// with v_off_i <= r < v_off_i + n_i, found once per row), and its lanes take
+// consecutive columns, so each load instruction of a warp reads one
+// contiguous piece of the row and each store writes one contiguous piece of
+// the rounded row (padding columns n_i .. ldq_i - 1 included).
+__device__ __forceinline__ int problem_of_row(const BDesc *d, int P, int r) {
     int lo = 0, hi = P - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (d[mid].g_off <= g) lo = mid;
+        if (d[mid].v_off <= r) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-// ---------------------------------------------------------------------------
-// Rounding of the packed matrices (Eq. 1, exact).
-// ---------------------------------------------------------------------------
-// Eight rounded values to the stored type: uint16 (padding 0x7FFF) or, when
-// floor(1/eps) <= 252, bytes (padding 0xFF).
-template <class CB>
-__device__ __forceinline__ void store8(CB *dst, const uint32_t h[8]) {
-    if (sizeof(CB) == 1)
-        *reinterpret_cast<uint2 *>(dst) = make_uint2(h[0] | (h[1] << 8) | (h[2] << 16) | (h[3] << 24),
-                                                     h[4] | (h[5] << 8) | (h[6] << 16) | (h[7] << 24));
-    else
-        *reinterpret_cast<uint4 *>(dst) =
-            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-}
-template <class CB> constexpr uint32_t kPadOf = sizeof(CB) == 1 ? 0xFFu : (uint32_t)kPadCost;
+// Columns per lane in flight per step of the matrix rounding: 2 KiB per warp
+// (16 FP32 or 8 FP64 values a lane), 64 KiB per SM at 32 warps, enough to
+// cover the load latency at the copy rate (1 KiB per warp reached 3.4 TB/s).
+template <class T> constexpr int kRowUnroll = sizeof(T) == 8 ? 8 : 16;
+// Columns per lane in flight per step of the points kernels.
+constexpr int kPtUnroll = 4;
 
+__device__ __forceinline__ uint32_t quantise_val(double x, const EpsSplit &e) {
+    const unsigned long long bits = __double_as_longlong(x);
+    return quantise_bits((uint32_t)(bits >> 32), (uint32_t)bits, e);
+}
+__device__ __forceinline__ uint32_t quantise_val(float x, const EpsSplit &e) {
+    return quantise_fbits(__float_as_uint(x), e);
+}
+
+// Eq. (1) on the packed matrices, exactly as k_quantise does for one problem.
 template <class T, class CB>
-__global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict__ d, int P,
-                                long long total_groups, EpsSplit e,
-                                CB *__restrict__ cb, WsHead *head) {
+__global__ void __launch_bounds__(256, 4) k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict__ d, int P, int total_rows,
+                                EpsSplit e, CB *__restrict__ cb, WsHead *head) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     bool bad = false;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int i = problem_of(d, P, g);
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total_rows; r += nw) {
+        const int i = problem_of_row(d, P, r);
         const BDesc D = d[i];
-        const long long lg = g - D.g_off;
-        const int gpr = D.ldq >> 3;
-        const int b = (int)(lg / gpr);
-        const int a0 = (int)(lg - (long long)b * gpr) << 3;
+        const int b = r - D.v_off;
         const T *row = C + D.c_off + (long long)b * D.n;
-        uint32_t h[8];
+        CB *out = cb + D.cb_off + (long long)b * D.ldq;
+        for (int a0 = 0; a0 < D.ldq; a0 += 32 * kRowUnroll<T>) {
+            T x[kRowUnroll<T>];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int a = a0 + j;
-            if (a < D.n) {
-                h[j] = quantise_elem(row, a, e);
-                if (h[j] == 0xFFFFFFFFu) {
-                    bad = true;
-                    h[j] = 0;
+            for (int u = 0; u < kRowUnroll<T>; ++u) {
+                const int a = a0 + 32 * u + lane;
+                x[u] = a < D.n ? __ldg(row + a) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kRowUnroll<T>; ++u) {
+                const int a = a0 + 32 * u + lane;
+                if (a >= D.ldq) break;
+                uint32_t q = kPadOf<CB>;
+                if (a < D.n) {
+                    q = quantise_val(x[u], e);
+                    if (q == 0xFFFFFFFFu) {
+                        bad = true;
+                        q = 0;
+                    }
                 }
-            } else {
-                h[j] = kPadOf<CB>;
+                out[a] = (CB)q;
             }
         }
-        store8<CB>(cb + D.cb_off + (long long)b * D.ldq + a0, h);
     }
     if (bad) record_error(head, PR_ERR_INVALID);
 }
@@ -155,58 +170,114 @@ __global__ void k_bquant_matrix(const T *__restrict__ C, const BDesc *__restrict
 // ---------------------------------------------------------------------------
 // Costs from points (points.cuh): c = RN32(d / max d) per problem.
 // ---------------------------------------------------------------------------
+// d(b, a) from b's coordinates held in registers, in the operation order of
+// dist_f32 (ascending k, one IEEE operation at a time); DIM > 0 is the
+// dimension known at compile time.
+template <int DIM>
+__device__ __forceinline__ float dist_regs(const float (&xb)[DIM], const float (&xa)[DIM], int squared) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float t = __fsub_rn(xb[k], xa[k]);
+        const float sq = __fmul_rn(t, t);
+        acc = k == 0 ? sq : __fadd_rn(acc, sq);
+    }
+    return squared ? acc : __fsqrt_rn(acc);
+}
+
+// Largest distance of every problem: a warp's maximum over one row, then one
+// atomic per row (non-negative floats order like their bit patterns).  DIM =
+// 0: any dimension, one column at a time; DIM > 0: each lane loads the
+// coordinates of kPtUnroll columns before it computes.
+template <int DIM>
 __global__ void k_bpoints_max(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
-                              int squared, const BDesc *__restrict__ d, int P,
-                              long long total_groups, unsigned *maxbits) {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int i = problem_of(d, P, g);
+                              int squared, const BDesc *__restrict__ d, int P, int total_rows,
+                              unsigned *maxbits) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total_rows; r += nw) {
+        const int i = problem_of_row(d, P, r);
         const BDesc D = d[i];
-        const long long lg = g - D.g_off;
-        const int gpr = D.ldq >> 3;
-        const int b = (int)(lg / gpr);
-        const int a0 = (int)(lg - (long long)b * gpr) << 3;
-        const float *xb = XB + (long long)(D.v_off + b) * dim;
+        const float *xbp = XB + (long long)r * dim;  // row b of problem i is global row r
         float m = 0.0f;
-        for (int j = 0; j < 8 && a0 + j < D.n; ++j)
-            m = fmaxf(m, dist_f32(xb, XA + (long long)(D.v_off + a0 + j) * dim, dim, squared));
-        // non-negative floats order like their bit patterns; one atomic per
-        // group of lanes working on the same problem
-        const unsigned active = __activemask();
-        const unsigned same = __match_any_sync(active, i);
-        const unsigned mx = __reduce_max_sync(same, __float_as_uint(m));
-        if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(maxbits + i, mx);
+        if (DIM == 0) {
+            for (int a = lane; a < D.n; a += 32)
+                m = fmaxf(m, dist_f32(xbp, XA + (long long)(D.v_off + a) * dim, dim, squared));
+        } else {
+            constexpr int DD = DIM > 0 ? DIM : 1;
+            float xb[DD];
+#pragma unroll
+            for (int k = 0; k < DD; ++k) xb[k] = xbp[k];
+            for (int a0 = 0; a0 < D.n; a0 += 32 * kPtUnroll) {
+                float xa[kPtUnroll][DD];
+#pragma unroll
+                for (int u = 0; u < kPtUnroll; ++u) {
+                    const int a = a0 + 32 * u + lane;
+                    const float *q = XA + (long long)(D.v_off + (a < D.n ? a : 0)) * DD;
+#pragma unroll
+                    for (int k = 0; k < DD; ++k) xa[u][k] = __ldg(q + k);
+                }
+#pragma unroll
+                for (int u = 0; u < kPtUnroll; ++u)
+                    if (a0 + 32 * u + lane < D.n) m = fmaxf(m, dist_regs<DD>(xb, xa[u], squared));
+            }
+        }
+        const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
+        if (lane == 0) atomicMax(maxbits + i, mx);
     }
 }
 
-template <class CB>
+template <int DIM, class CB>
 __global__ void k_bpoints_quant(const float *__restrict__ XA, const float *__restrict__ XB, int dim,
-                                int squared, const BDesc *__restrict__ d, int P,
-                                long long total_groups, const unsigned *__restrict__ maxbits,
-                                EpsSplit e, CB *__restrict__ cb) {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_groups;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int i = problem_of(d, P, g);
+                                int squared, const BDesc *__restrict__ d, int P, int total_rows,
+                                const unsigned *__restrict__ maxbits, EpsSplit e, CB *__restrict__ cb) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total_rows; r += nw) {
+        const int i = problem_of_row(d, P, r);
         const BDesc D = d[i];
-        const long long lg = g - D.g_off;
-        const int gpr = D.ldq >> 3;
-        const int b = (int)(lg / gpr);
-        const int a0 = (int)(lg - (long long)b * gpr) << 3;
+        const int b = r - D.v_off;
         const float M = __uint_as_float(maxbits[i]);
-        const float *xb = XB + (long long)(D.v_off + b) * dim;
-        uint32_t h[8];
+        const float *xbp = XB + (long long)r * dim;
+        CB *out = cb + D.cb_off + (long long)b * D.ldq;
+        if (DIM == 0) {
+            for (int a = lane; a < D.ldq; a += 32) {
+                uint32_t q = kPadOf<CB>;
+                if (a < D.n) {
+                    const float dd = dist_f32(xbp, XA + (long long)(D.v_off + a) * dim, dim, squared);
+                    const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
+                    q = quantise_fbits(__float_as_uint(c), e);
+                }
+                out[a] = (CB)q;
+            }
+        } else {
+            constexpr int DD = DIM > 0 ? DIM : 1;
+            float xb[DD];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int a = a0 + j;
-            if (a < D.n) {
-                const float dd = dist_f32(xb, XA + (long long)(D.v_off + a) * dim, dim, squared);
-                const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
-                h[j] = quantise_fbits(__float_as_uint(c), e);
-            } else {
-                h[j] = kPadOf<CB>;
+            for (int k = 0; k < DD; ++k) xb[k] = xbp[k];
+            for (int a0 = 0; a0 < D.ldq; a0 += 32 * kPtUnroll) {
+                float xa[kPtUnroll][DD];
+#pragma unroll
+                for (int u = 0; u < kPtUnroll; ++u) {
+                    const int a = a0 + 32 * u + lane;
+                    const float *q = XA + (long long)(D.v_off + (a < D.n ? a : 0)) * DD;
+#pragma unroll
+                    for (int k = 0; k < DD; ++k) xa[u][k] = __ldg(q + k);
+                }
+#pragma unroll
+                for (int u = 0; u < kPtUnroll; ++u) {
+                    const int a = a0 + 32 * u + lane;
+                    if (a >= D.ldq) break;
+                    uint32_t q = kPadOf<CB>;
+                    if (a < D.n) {
+                        const float dd = dist_regs<DD>(xb, xa[u], squared);
+                        const float c = M > 0.0f ? __fdiv_rn(dd, M) : 0.0f;
+                        q = quantise_fbits(__float_as_uint(c), e);
+                    }
+                    out[a] = (CB)q;
+                }
             }
         }
-        store8<CB>(cb + D.cb_off + (long long)b * D.ldq + a0, h);
     }
 }
 
@@ -539,7 +610,7 @@ __global__ void k_binit(BCtl *ctl, unsigned *maxbits, int P) {
 struct Plan {
     std::vector<BDesc> desc;
     std::vector<int> order;
-    long long cb_elems = 0, groups = 0, c_elems = 0;
+    long long cb_elems = 0, c_elems = 0;
     int n_max = 0, ldq_max = 0, v_total = 0;
 };
 
@@ -547,7 +618,7 @@ pr_status make_plan(int P, const int32_t *n_host, double eps, Plan &pl) {
     if (P < 1) return fail(PR_ERR_INVALID, "batched: n_problems must be >= 1");
     if (!n_host) return fail(PR_ERR_INVALID, "batched: NULL size array");
     pl.desc.resize(P);
-    long long cb = 0, g = 0, c = 0;
+    long long cb = 0, c = 0;
     long long v = 0;
     const long long K = eps > 0 ? (long long)floor(1.0 / eps) : 0;
     for (int i = 0; i < P; ++i) {
@@ -558,20 +629,17 @@ pr_status make_plan(int P, const int32_t *n_host, double eps, Plan &pl) {
         d.ldq = (n + 15) & ~15;  // rows start on 16 bytes in either storage type
         d.cb_off = cb;
         d.c_off = c;
-        d.g_off = g;
         d.v_off = (int)v;
         d.T = (int)floor(eps * (double)n);
         d.cap = ((long long)n * (2 * K + 3)) / (d.T + 1) + 1;
         cb += (long long)n * d.ldq;
         c += (long long)n * n;
-        g += (long long)n * (d.ldq >> 3);
         v += n;
         pl.n_max = std::max(pl.n_max, n);
         pl.ldq_max = std::max(pl.ldq_max, d.ldq);
     }
     if (v > (1ll << 30)) return fail(PR_ERR_INVALID, "batched: too many rows in total");
     pl.cb_elems = cb;
-    pl.groups = g;
     pl.c_elems = c;
     pl.v_total = (int)v;
     pl.order.resize(P);
@@ -632,30 +700,47 @@ pr_status run_batched(const Source &src, int32_t P, const int32_t *n_host, doubl
     PR_CUDA(cudaMemcpyAsync(d_order, pl.order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
 
     const EpsSplit e = make_eps_split(eps);
-    const long long want = pl.groups / 256 + 1;
-    const int qgrid = (int)std::min<long long>(want, (long long)di.sms * 16);
+    // a warp per row: 4 CTAs of 8 warps per SM (all resident at up to 64
+    // registers a thread), fewer when there are fewer rows
+    const int qgrid = std::max(1, std::min(di.sms * 4, (pl.v_total + 7) / 8));
     if (src.points) {
-        k_bpoints_max<<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P, pl.groups, d_max);
-        PR_CUDA(cudaGetLastError());
-        if (cb8)
-            k_bpoints_quant<uint8_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P,
-                                                            pl.groups, d_max, e, (uint8_t *)d_cb);
-        else
-            k_bpoints_quant<uint16_t><<<qgrid, 256, 0, st>>>(src.XA, src.XB, src.dim, src.squared, d_desc, P,
-                                                             pl.groups, d_max, e, (uint16_t *)d_cb);
+        // two and three dimensions have their own kernels (coordinates in
+        // registers, several columns' loads in flight); any other runs the
+        // column-at-a-time form
+        const int D = src.dim == 2 ? 2 : src.dim == 3 ? 3 : 0;
+        const void *kmax = D == 2 ? (const void *)k_bpoints_max<2> : D == 3 ? (const void *)k_bpoints_max<3>
+                                                                              : (const void *)k_bpoints_max<0>;
+        const void *kq = cb8 ? (D == 2 ? (const void *)k_bpoints_quant<2, uint8_t>
+                                : D == 3 ? (const void *)k_bpoints_quant<3, uint8_t>
+                                         : (const void *)k_bpoints_quant<0, uint8_t>)
+                             : (D == 2 ? (const void *)k_bpoints_quant<2, uint16_t>
+                                : D == 3 ? (const void *)k_bpoints_quant<3, uint16_t>
+                                         : (const void *)k_bpoints_quant<0, uint16_t>);
+        int dim_ = src.dim, sq_ = src.squared, P_ = P, rows_ = pl.v_total;
+        const float *xa_ = src.XA, *xb_ = src.XB;
+        const BDesc *dd_ = d_desc;
+        unsigned *mx_ = d_max;
+        void *amax[] = {(void *)&xa_, (void *)&xb_, (void *)&dim_, (void *)&sq_, (void *)&dd_, (void *)&P_,
+                        (void *)&rows_, (void *)&mx_};
+        PR_CUDA(cudaLaunchKernel(kmax, dim3(qgrid), dim3(256), amax, 0, st));
+        const unsigned *cmx_ = d_max;
+        void *cbp_ = d_cb;
+        void *aq[] = {(void *)&xa_, (void *)&xb_, (void *)&dim_, (void *)&sq_, (void *)&dd_, (void *)&P_,
+                      (void *)&rows_, (void *)&cmx_, (void *)&e, (void *)&cbp_};
+        PR_CUDA(cudaLaunchKernel(kq, dim3(qgrid), dim3(256), aq, 0, st));
     } else if (src.dt == PR_F64) {
         if (cb8)
-            k_bquant_matrix<double, uint8_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups, e,
+            k_bquant_matrix<double, uint8_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.v_total, e,
                                                                     (uint8_t *)d_cb, &ctl->head);
         else
-            k_bquant_matrix<double, uint16_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.groups,
+            k_bquant_matrix<double, uint16_t><<<qgrid, 256, 0, st>>>((const double *)src.C, d_desc, P, pl.v_total,
                                                                      e, (uint16_t *)d_cb, &ctl->head);
     } else {
         if (cb8)
-            k_bquant_matrix<float, uint8_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
+            k_bquant_matrix<float, uint8_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.v_total, e,
                                                                    (uint8_t *)d_cb, &ctl->head);
         else
-            k_bquant_matrix<float, uint16_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.groups, e,
+            k_bquant_matrix<float, uint16_t><<<qgrid, 256, 0, st>>>((const float *)src.C, d_desc, P, pl.v_total, e,
                                                                     (uint16_t *)d_cb, &ctl->head);
     }
     PR_CUDA(cudaGetLastError());

@@ -67,6 +67,27 @@ def test_points_batch_matches_oracle(prot, eps):
         check_problem(got, i, int(s), int(n), ref)
 
 
+@pytest.mark.parametrize("dim,metric", [(2, "euclidean"), (5, "sqeuclidean"), (1, "euclidean")])
+def test_points_other_dimensions(prot, dim, metric):
+    """Two dimensions (its own kernel), and five and one (the kernel for any
+    dimension): the same costs, bit for bit, as the oracle's point solve."""
+    import torch
+    sizes = W.batched_sizes(12, 33, 400, seed=dim)
+    g = np.random.default_rng(100 + dim)
+    total = int(np.sum(sizes))
+    XA = g.random((total, dim)).astype(np.float32)
+    XB = g.random((total, dim)).astype(np.float32)
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    got = prot.assign_batched_points(torch.from_numpy(XA).cuda(), torch.from_numpy(XB).cuda(),
+                                     sizes, 0.02, metric=metric)
+    got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in got.items()}
+    for i, n in enumerate(sizes):
+        s, e = off[i], off[i + 1]
+        ref = OP.assign_points(XA[s:e], XB[s:e], 0.02, squared=metric == "sqeuclidean")
+        check_problem(got, i, int(s), int(n), ref)
+
+
 def test_points_euclidean_and_float32_matrix(prot):
     import torch
     sizes = np.array([100, 257, 64], np.int32)
