@@ -48,6 +48,8 @@ def parse():
                     help="skip the eps sweep, batched, autograd and OT measurements")
     ap.add_argument("--ot-once", action="store_true",
                     help="only the OT workload: two warm solves, then --steps timed ones (profiling runs)")
+    ap.add_argument("--batched-once", action="store_true",
+                    help="only the batched workload: one warm call each, then --steps timed ones (profiling runs)")
     return ap.parse_args()
 
 
@@ -304,6 +306,50 @@ def timed(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def run_batched(a, torch, prot, W, dev, stream, reps=3, plain=True):
+    """Batched: 512 problems, n_i uniform in [64, 2048], 3-D points, squared
+    Euclidean / max, eps = 0.01, solved in one launch from the points and from
+    the same problems as FP32 cost matrices (CUDA events over `reps` calls of
+    each); with `plain`, also one pr_assign launch per problem."""
+    sizes = W.batched_sizes(512, 64, 2048, seed=0)
+    XA, XB, off = W.batched_points_3d(sizes, seed=0)
+    XAd, XBd = torch.from_numpy(XA).to(dev), torch.from_numpy(XB).to(dev)
+    wsb = prot.Workspace(dev)
+    res = prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb)
+    outb = {k: v for k, v in res.items() if k != "stats"}
+    ms_pts = timed(torch, stream, lambda: prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb,
+                                                                      sync=False, out=outb), reps)
+    mats = []
+    for i in range(len(sizes)):
+        xa, xb = XAd[off[i]:off[i + 1]], XBd[off[i]:off[i + 1]]
+        d = ((xb[:, None, :] - xa[None, :, :]) ** 2).sum(-1)
+        mats.append((d / d.max()).contiguous())
+    packed = torch.cat([m.reshape(-1) for m in mats])
+    resm = prot.assign_batched(packed, sizes, 0.01, ws=wsb)
+    outm = {k: v for k, v in resm.items() if k != "stats"}
+    ms_mat = timed(torch, stream, lambda: prot.assign_batched(packed, sizes, 0.01, ws=wsb, sync=False,
+                                                               out=outm), reps)
+    P = len(sizes)
+    out = {"workload": "512 problems, n_i ~ U{64..2048}, 3-D uniform points, squared Euclidean / max, eps=0.01",
+           "problems_per_s_points": P / (ms_pts * 1e-3),
+           "problems_per_s_matrix": P / (ms_mat * 1e-3),
+           "ms_points": ms_pts, "ms_matrix": ms_mat,
+           "phases_total": int(res["stats"]["phases"]), "bytes_scanned": res["stats"]["bytes_scanned"]}
+    if plain:
+        wsp = prot.Workspace(dev)
+        outs = [None] * len(mats)
+
+        def one_launch_per_problem():
+            for i, m in enumerate(mats):
+                r = prot.assign(m, 0.01, ws=wsp, sync=False, out=outs[i])
+                outs[i] = {k: v for k, v in r.items() if k != "stats"}
+        one_launch_per_problem()
+        ms_plain = timed(torch, stream, one_launch_per_problem, 1)
+        out.update({"problems_per_s_plain": P / (ms_plain * 1e-3), "ms_plain_512_launches": ms_plain,
+                    "speedup_vs_plain": ms_plain / ms_mat})
+    return out
+
+
 def run_extras(a, torch, prot, W, dev, stream):
     """The other measurements of the headline metric, each bounded in time."""
     import numpy as np
@@ -351,44 +397,7 @@ def run_extras(a, torch, prot, W, dev, stream):
                            "phases": r["stats"]["phases"], "cells_examined": r["stats"]["cells_examined"]}
     del XA, XB, XA2, XB2
 
-    # batched: 512 problems, n_i uniform in [64, 2048], 3-D points, sq. Euclidean, eps 0.01
-    sizes = W.batched_sizes(512, 64, 2048, seed=0)
-    XA, XB, off = W.batched_points_3d(sizes, seed=0)
-    XAd, XBd = torch.from_numpy(XA).to(dev), torch.from_numpy(XB).to(dev)
-    wsb = prot.Workspace(dev)
-    res = prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb)
-    outb = {k: v for k, v in res.items() if k != "stats"}
-    ms_pts = timed(torch, stream, lambda: prot.assign_batched_points(XAd, XBd, sizes, 0.01, ws=wsb,
-                                                                      sync=False, out=outb), 3)
-    # the same problems as FP32 cost matrices: one batched launch vs one launch per problem
-    mats = []
-    for i in range(len(sizes)):
-        xa, xb = XAd[off[i]:off[i + 1]], XBd[off[i]:off[i + 1]]
-        d = ((xb[:, None, :] - xa[None, :, :]) ** 2).sum(-1)
-        mats.append((d / d.max()).contiguous())
-    packed = torch.cat([m.reshape(-1) for m in mats])
-    resm = prot.assign_batched(packed, sizes, 0.01, ws=wsb)
-    outm = {k: v for k, v in resm.items() if k != "stats"}
-    ms_mat = timed(torch, stream, lambda: prot.assign_batched(packed, sizes, 0.01, ws=wsb, sync=False,
-                                                               out=outm), 3)
-    wsp = prot.Workspace(dev)
-    outs = [None] * len(mats)
-
-    def plain():
-        for i, m in enumerate(mats):
-            r = prot.assign(m, 0.01, ws=wsp, sync=False, out=outs[i])
-            outs[i] = {k: v for k, v in r.items() if k != "stats"}
-    plain()
-    ms_plain = timed(torch, stream, plain, 1)
-    P = len(sizes)
-    ex["batched"] = {"workload": "512 problems, n_i ~ U{64..2048}, 3-D uniform points, squared Euclidean / max, eps=0.01",
-                     "problems_per_s_points": P / (ms_pts * 1e-3),
-                     "problems_per_s_matrix": P / (ms_mat * 1e-3),
-                     "problems_per_s_plain": P / (ms_plain * 1e-3),
-                     "ms_points": ms_pts, "ms_matrix": ms_mat, "ms_plain_512_launches": ms_plain,
-                     "speedup_vs_plain": ms_plain / ms_mat,
-                     "phases_total": int(res["stats"]["phases"]), "bytes_scanned": res["stats"]["bytes_scanned"]}
-    del packed, mats, outs
+    ex["batched"] = run_batched(a, torch, prot, W, dev, stream)
 
     # autograd: 64 pairs, n = 4096, d = 3, N(0,1), squared Euclidean, eps 0.01
     X, Y = W.cloud_pairs_normal(64, 4096, 3, seed=0)
@@ -605,6 +614,11 @@ def main():
     torch.cuda.set_device(local)
     if a.ot_once:
         print(json.dumps({"ot": run_ot(a, torch, prot, W, torch.device("cuda", local), reps=max(1, a.steps))}))
+        return
+    if a.batched_once:
+        dev1 = torch.device("cuda", local)
+        print(json.dumps({"batched": run_batched(a, torch, prot, W, dev1, torch.cuda.current_stream(dev1),
+                                                 reps=max(1, a.steps), plain=False)}))
         return
     dist = None
     if world > 1:
