@@ -111,6 +111,35 @@ def test_points_euclidean_and_float32_matrix(prot):
         assert np.array_equal(got2["y_row"].cpu().numpy()[s:s + n], ref["y_row"])
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_matrix_batch_sixteen_bit_storage(prot, dtype):
+    """eps = 0.003 (floor(1/eps) = 333 > 252): the matrix rounding writes
+    16-bit values; FP64 and FP32 matrices, sizes with ragged rows."""
+    import torch
+    sizes = np.array([5, 63, 130, 301], np.int32)
+    eps = 0.003
+    mats = [W.assignment_euclid_2d(int(n), 70 + i).astype(dtype) for i, n in enumerate(sizes)]
+    packed = np.concatenate([m.ravel() for m in mats])
+    got = prot.assign_batched(torch.from_numpy(packed).cuda(), sizes, eps)
+    got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in got.items()}
+    off = 0
+    for i, n in enumerate(sizes):
+        check_problem(got, i, off, int(n), oracle.assign(mats[i], eps))
+        off += int(n)
+
+
+def test_matrix_batch_refuses_a_cost_out_of_range(prot):
+    """One cost above 1 in one problem of the batch: PR_ERR_INVALID."""
+    import torch
+    sizes = np.array([40, 70, 33], np.int32)
+    mats = [W.assignment_euclid_2d(int(n), 90 + i) for i, n in enumerate(sizes)]
+    mats[1][17, 5] = 1.5
+    packed = np.concatenate([m.ravel() for m in mats])
+    with pytest.raises(prot.PrError) as e:
+        prot.assign_batched(torch.from_numpy(packed).cuda(), sizes, 0.05)
+    assert e.value.status == -1
+
+
 def test_batch_equals_single_problem_solver(prot):
     """Closed form (v): each batched result equals pr_assign on that problem."""
     import torch
