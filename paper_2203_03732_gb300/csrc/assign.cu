@@ -182,6 +182,9 @@ __global__ void k_init(Params p, int *match_b) {
         if (a < p.nA) p.prop[a] = word_of(0, -1);  // round 0, no partner
     }
     for (int i = t0; i < 3 * p.won_words; i += stride) p.won[i] = 0;
+    // every pool slot free (y = 0, see pool_take)
+    unsigned long long *pool = reinterpret_cast<unsigned long long *>(p.pool);
+    for (long long i = t0; i < 2ll * p.nB; i += stride) pool[i] = 0;
     if (t0 == 0) {
         Ctl *c = p.ctl;
         memset(c, 0, sizeof(Ctl));
@@ -304,6 +307,43 @@ __device__ __forceinline__ void push_next(Smem &s, int nxt, int keep, int b, int
     atomicAdd(&s.nf_delta, 1);
 }
 
+// Pool entries: one 64-bit word (b, y), stored and loaded whole.  A real entry
+// never has y = 0 (a relabelled row carries y(b) >= 1, an evicted row -2 - a),
+// so 0 marks a free slot: k_init clears the pool, and the CTA that takes an
+// entry at a phase start clears it again (the slot is written next two phases
+// later, behind at least one grid barrier).
+__device__ __forceinline__ void pool_put(int2 *pool, long long k, int2 e) {
+    const unsigned long long v = ((unsigned long long)(unsigned)e.y << 32) | (unsigned)e.x;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(reinterpret_cast<unsigned long long *>(pool) + k),
+                 "l"(v)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long pool_raw(const int2 *pool, long long k) {
+    return ld_relaxed_u64(reinterpret_cast<const unsigned long long *>(pool) + k);
+}
+// Takes entry k of this phase's pool given `raw` (an earlier load of it): a
+// free slot means the entry was written after its CTA arrived at the phase's
+// last barrier (grid_sync_pool) and has not reached L2 yet, so it is loaded
+// again, for at most `limit` cycles.  False (and PR_ERR_TIMEOUT) if it never
+// arrives.
+__device__ __forceinline__ bool pool_take(int2 *pool, long long k, unsigned long long raw, long long limit,
+                                          Ctl *ctl, int &b, int &y) {
+    if ((unsigned)(raw >> 32) == 0u) {
+        const long long t0 = clock64();
+        do {
+            if (clock64() - t0 > limit) {
+                record_error(&ctl->head, PR_ERR_TIMEOUT);
+                return false;
+            }
+            raw = pool_raw(pool, k);
+        } while ((unsigned)(raw >> 32) == 0u);
+    }
+    b = (int)(unsigned)raw;
+    y = (int)(raw >> 32);
+    pool_put(pool, k, make_int2(0, 0));
+    return true;
+}
+
 // Grid barrier carrying a payload.  Barrier h adds, for each CTA,
 //   1 (arrival) | had_prop << 10 | nonfirst << 20 | nf_delta << 40
 // (had_prop, nonfirst in {0,1}; nf_delta < 2^24; at most 1023 CTAs) to word 0
@@ -348,6 +388,62 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, Smem &s, unsigned &gen, unsi
         const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
         s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
         s.pub2 = !ok ? 0 : all_to_pool ? ((v >> 40) & 0xFFFFFFull) : ld_relaxed_u64(slot + 1);
+        s.err = ok ? 0 : 1;
+    }
+    __syncthreads();
+    gen += 1;
+    return s.err == 0;
+}
+
+// grid_sync when every next-phase row goes to the pool and a CTA's donations
+// of a round fit its shared-memory buffer.  The arrival is an atomic that
+// returns the slot's previous value: its nf_delta field (the donations of the
+// CTAs that arrived before this one) places this CTA's donations in the pool
+// after those of the earlier rounds (pool_base), with no reservation before
+// the barrier; the CTA then writes them and waits.  A CTA whose
+// arrival completes the count has seen every other arrival (the atomic
+// acquires) and does not poll.  Entries written after the last arrival may
+// reach L2 after another CTA passed the barrier: pool_take waits for them.
+__device__ __forceinline__ bool grid_sync_pool(Ctl *ctl, Smem &s, unsigned &gen, unsigned G, long long limit,
+                                               unsigned long long mine, int2 *pool_next, long long pool_base) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned h = gen + 1;
+        unsigned long long *slot = ctl->bar_slot[h & 3];
+        if (blockIdx.x == 0) {
+            ctl->bar_slot[(h + 2) & 3][0] = 0;
+            ctl->bar_slot[(h + 2) & 3][1] = 0;
+        }
+        unsigned long long old;
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(slot), "l"(mine) : "memory");
+        s.don_base = (int)(pool_base + (long long)((old >> 40) & 0xFFFFFFull));
+        s.pub2 = old + mine;  // the slot right after this arrival
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < s.ndon; i += blockDim.x) pool_put(pool_next, s.don_base + i, s.don[i]);
+    if (threadIdx.x == 0) {
+        unsigned long long *slot = ctl->bar_slot[(gen + 1) & 3];
+        unsigned long long v = s.pub2;
+        bool ok = true;
+        if ((v & 1023ull) != (unsigned long long)G) {
+            const long long t0 = clock64();
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(slot) : "memory");
+                if ((v & 1023ull) == (unsigned long long)G) break;
+                if (ld_relaxed_s32(&ctl->head.abort)) {
+                    ok = false;
+                    break;
+                }
+                if (clock64() - t0 > limit) {
+                    record_error(&ctl->head, PR_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        const unsigned long long P = (v >> 10) & 1023ull, L = (v >> 20) & 1023ull;
+        s.pub = ((P ? 1ull : 0ull) << 31) | ((L ? 1ull : 0ull) << 30) | ((v >> 40) & 0xFFFFFFull);
+        s.pub2 = ok ? ((v >> 40) & 0xFFFFFFull) : 0;
         s.err = ok ? 0 : 1;
     }
     __syncthreads();
@@ -504,7 +600,7 @@ template <class CB, bool SL, bool F7, bool OFS>
 __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &p,
                                          const CB *ks, const unsigned *tk, unsigned *won_now,
                                          unsigned R, unsigned Rps, int nxt, int qcur, int keep,
-                                         int2 *pool_next, int *pool_cnt, int warps_per_row,
+                                         int2 *pool_next, int *pool_cnt, bool defer_don, int warps_per_row,
                                          int rows_per_group, unsigned char *slots, unsigned &mstate,
                                          unsigned long long &cells) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -646,10 +742,11 @@ __device__ __forceinline__ void run_jobs(Smem &s, const Lists &g, const Params &
     }
     __syncthreads();
     const unsigned long long tC = p.profile ? ptimer() : 0;
-    if (s.ndon > 0) {
+    // donations (unless grid_sync_pool places them at the barrier)
+    if (!defer_don && s.ndon > 0) {
         if (threadIdx.x == 0) s.don_base = atomicAdd(pool_cnt, s.ndon);
         __syncthreads();
-        for (int i = threadIdx.x; i < s.ndon; i += blockDim.x) pool_next[s.don_base + i] = s.don[i];
+        for (int i = threadIdx.x; i < s.ndon; i += blockDim.x) pool_put(pool_next, s.don_base + i, s.don[i]);
         __syncthreads();
         if (threadIdx.x == 0) {
             s.donated += s.ndon;
@@ -713,6 +810,10 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
     // goes to the pool, which deals them out evenly (measured at n = 10,000:
     // 1-3 % faster than keeping one); shorter rows keep up to a group's worth.
     const int keep = rows_per_group > 2 ? min(rows_per_group - 1, kKeepMax) : 0;
+    // Every next-phase row goes to the pool and no CTA takes more than kBatch
+    // rows in a round (so its donations of a round fit s.don): the barrier
+    // places the donations (grid_sync_pool).
+    const bool place_at_barrier = !CL && keep == 0 && p.nB <= kBatch * (int)G;
     Lists g;
     int *base = p.lists + (size_t)cta * p.list_stride;
     g.ql[0] = reinterpret_cast<int4 *>(base);
@@ -765,7 +866,7 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
         // ---- one phase ----
         const unsigned Rps = R + 1;
         const int pq = (int)(phase & 1);
-        const int2 *pool_now = p.pool + (size_t)pq * p.nB;
+        int2 *pool_now = p.pool + (size_t)pq * p.nB;
         int2 *pool_next = p.pool + (size_t)(pq ^ 1) * p.nB;
         if (cta == 0 && threadIdx.x == 0) ctl->pool_cnt[pq] = 0;  // for phase + 1's donations
         const int kept = phase == 0 ? first_items : min(s.nfl[cur], keep);
@@ -782,20 +883,21 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 s.nonfirst = 0;
                 s.nf_delta = 0;
                 s.donated = 0;
+                s.ndon = 0;
                 s.nql[qcur] = 0;
             }
             // items of this round: kept rows + pool share, or last round's proposals
             const int nitems = first_round ? kept + from_pool : s.nql[qcur ^ 1];
             // Issue this thread's first item load and its bitmap-word load
             // before using either, so the two global reads overlap.
-            int2 pre_pool = make_int2(0, 0);
+            unsigned long long pre_pool = 0;
             unsigned long long pre_word = 0;
             int4 pre_q = make_int4(0, 0, 0, 0);
             const int it0 = threadIdx.x;
             if (it0 < nitems && it0 < kBatch) {
                 if (first_round) {
                     if (phase > 0 && it0 >= kept)
-                        pre_pool = ld_relaxed_int2(pool_now + cta + (long long)(it0 - kept) * G);
+                        pre_pool = pool_raw(pool_now, cta + (long long)(it0 - kept) * G);
                 } else {
                     pre_q = ql_get(s, g, qcur ^ 1, it0);
                     pre_word = ld_relaxed_u64(p.prop + pre_q.y);
@@ -846,9 +948,9 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                             b = e.x;
                             y = e.y;
                         } else {
-                            const int2 e = pre ? pre_pool : ld_relaxed_int2(pool_now + cta + (long long)(it - kept) * G);
-                            b = e.x;
-                            y = e.y;
+                            const long long k = cta + (long long)(it - kept) * G;
+                            if (!pool_take(pool_now, k, pre ? pre_pool : pool_raw(pool_now, k), p.spin_limit, ctl, b, y))
+                                continue;  // PR_ERR_TIMEOUT: the kernel stops at the next barrier
                         }
                         if (y < 0) {  // an evicted row: y(b) unknown, resume point -1 - y
                             start = -1 - y;
@@ -893,7 +995,8 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                 __syncthreads();
                 if (p.profile && threadIdx.x == 0) s.pacc[0] += ptimer() - t_mark;
                 run_jobs<CB, SL, F7, OFS>(s, g, p, ks, tk, won_now, R, Rps, cur ^ 1, qcur, keep, pool_next,
-                                 &ctl->pool_cnt[pq ^ 1], warps_per_row, rows_per_group, slots, mstate, cells);
+                                          &ctl->pool_cnt[pq ^ 1], place_at_barrier, warps_per_row, rows_per_group,
+                                          slots, mstate, cells);
                 if (p.profile) t_mark = ptimer();
             }
             const unsigned long long mine = 1ull | ((unsigned long long)s.had_prop << 10) |
@@ -916,9 +1019,11 @@ k_phases(Params p, int warps_per_row, int rows_per_group) {
                     for (int k = 0; k < kProfSegs; ++k) ctl->prof_slot[(R + 1) & 1][k] = 0;
                 }
             }
-            const bool synced = CL ? cluster_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)
-                                   : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated,
-                                               keep == 0);
+            const bool synced =
+                CL ? cluster_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated)
+                : place_at_barrier
+                    ? grid_sync_pool(ctl, s, gen, G, p.spin_limit, mine, pool_next, pool_next_size)
+                    : grid_sync(ctl, s, gen, G, p.spin_limit, mine, (unsigned long long)s.donated, keep == 0);
             if (!synced) goto done;
             if (p.profile && threadIdx.x == 0) {
                 seg[5] = ptimer() - t_r2;
