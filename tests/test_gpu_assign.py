@@ -393,3 +393,17 @@ def test_pinned_host_costs_read_in_place(prot):
     assert rc == _lib.PR_ERR_INVALID
     assert b"pinned host memory" in L.pr_last_error()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("nB,nA,eps", [(3900, 3900, 0.003), (8000, 8000, 0.02), (6000, 9500, 0.01)])
+def test_barrier_places_the_pool(prot, monkeypatch, nB, nA, eps):
+    """Rows long enough that no CTA keeps rows for its next phase, so the grid
+    barrier's arrival places each CTA's pool donations and a reader may find
+    a slot still free and wait for it: 16-bit storage (eps = 0.003), bytes,
+    and more columns than rows; bit-exact with the oracle, entries examined
+    included."""
+    set_form(monkeypatch, "grid")
+    C = W.assignment_euclid_2d(nB, 7 + nB, n_a=nA)
+    got = gpu_solve(prot, C, eps)
+    assert_parity(got, oracle.assign(C, eps))
+    assert_cells(got, C, eps)
