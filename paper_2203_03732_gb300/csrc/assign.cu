@@ -1415,7 +1415,7 @@ pr_status phase_cfg(PhaseCfg &cfg) {
 // distributed shared memory, about a third of a grid barrier's latency) or
 // on the whole grid (one CTA per SM, barriers through L2).  PR_PHASE_MODE =
 // "grid" or "cluster" forces one; otherwise the cluster runs problems of up
-// to kClusterMaxRows rows.
+// to kClusterMaxRows rows with floor(1/eps) > kClusterMinK.
 // Cluster mode also needs at least kMinSlots row slots next to the keys.
 constexpr int kMinSlots = 4;
 
@@ -1423,13 +1423,18 @@ constexpr int kMinSlots = 4;
 // rows (n = 2000: 15 %, n = 4000: 6 %); at n = 10,000 the 16 SMs' scan
 // throughput falls behind the whole grid's (37 % slower).
 constexpr int kClusterMaxRows = 4096;
+// ... and only when floor(1/eps) > 20: at larger eps a solve is one phase of
+// many rounds with many rows, where the whole grid's scans win (eps = 0.1:
+// n = 1000 0.152 vs 0.169 ms, n = 3000 0.333 vs 0.505 ms, grid vs cluster;
+// eps = 0.01: 8.24 vs 7.42 ms and 1.97 vs 1.99 ms).
+constexpr long long kClusterMinK = 20;
 
-bool use_cluster(const PhaseCfg &cfg, int nslots, int n_rows) {
+bool use_cluster(const PhaseCfg &cfg, int nslots, int n_rows, long long K) {
     if (cfg.cluster < 1 || nslots < kMinSlots) return false;
     const char *m = getenv("PR_PHASE_MODE");
     if (m && strcmp(m, "grid") == 0) return false;
     if (m && strcmp(m, "cluster") == 0) return true;
-    return n_rows <= kClusterMaxRows;
+    return n_rows <= kClusterMaxRows && K > kClusterMinK;
 }
 
 // Row scans of the grid form: a CTA with more jobs than one register group
@@ -1602,7 +1607,7 @@ pr_status launch_solve(Params &p, const CostSource &src, double eps, const Phase
     const int kb = cb8 ? 1 : 2;  // bytes per key in the shared-memory copy
     const size_t slot_room = cfg.smem > slots_offset(p.ldq, kb) ? cfg.smem - slots_offset(p.ldq, kb) : 0;
     p.nslots = (int)std::min<size_t>((size_t)kWarps, slot_room / (size_t)p.slot_bytes);
-    const bool cluster = p.rule <= PR_RULE_OFFSET && use_cluster(cfg, p.nslots, n_rows);
+    const bool cluster = p.rule <= PR_RULE_OFFSET && use_cluster(cfg, p.nslots, n_rows, K);
     if (p.rule == PR_RULE_SEQUENTIAL) {
         // the phase's keys live in shared memory, one per column (the size
         // was checked by pr_assign_rule)
